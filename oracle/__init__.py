@@ -1,0 +1,172 @@
+"""CPU oracle for the water-flow constrained shortest path method (arXiv 1511.06441).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline of ``bench.py`` import this package.  The product (``paper_1511_06441_gb300``)
+never imports it, and it imports nothing from the product.
+
+The solvers live in ``csp_oracle.c`` (plain C, compiled here with gcc on first use):
+
+* :func:`cycle`  - O1, the paper's cycle loop (Algorithm 1, Steps 1-9), with trace;
+* :func:`pareto` - O2, an independent Dijkstra over (vertex, quality) states;
+* :func:`lexmin` - unconstrained lexicographic (F1, F2) Dijkstra (input preparation).
+
+Parity unpinned: nothing.  Every output is pinned by the tests against brute force,
+plain Dijkstra, closed forms or the paper's Lemma; see the C file's header.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "csp_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, INVALID, OOM, TIMEOUT = 0, 1, 2, 5
+
+
+def build(force: bool = False) -> str:
+    """Compile ``csp_oracle.c`` into ``liboracle.so`` (gcc -O2, portable flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            lib.oracle_cycle.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, i64p,
+                                         i64p, ctypes.c_int64, i64p, ctypes.c_int64, i64p, i64p, i64p]
+            lib.oracle_pareto.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
+                                          ctypes.c_int64, ctypes.c_int64, i64p]
+            lib.oracle_lexmin.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
+                                          ctypes.c_int64, i64p]
+            for f in (lib.oracle_cycle, lib.oracle_pareto, lib.oracle_lexmin):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p64(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _p32(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__(f"oracle returned status {code}")
+        self.code = code
+
+
+@dataclasses.dataclass
+class Result:
+    F1: int
+    X: int
+    x_src: int
+    x_dir: int
+    F2: int
+    cycles: int = -1
+    updates: int = -1          # sum over cycles of the flows alive at cycle start
+    launched: int = -1         # flows started (including phantoms)
+    trace: Optional[np.ndarray] = None     # (rows, 3) int64: Time, active vertices, flows
+    labels: Optional[np.ndarray] = None    # (V,) int64 labels at termination
+    snapshot: Optional[np.ndarray] = None  # active vertex ids at the requested time
+
+    def answer(self):
+        return (self.F1, self.X, self.x_src, self.x_dir, self.F2)
+
+
+def _common(extents, f1, f2, A, B):
+    ext = np.ascontiguousarray(np.asarray(extents, dtype=np.int64))
+    f1 = np.ascontiguousarray(np.asarray(f1).astype(np.int32).reshape(-1))
+    f2 = np.ascontiguousarray(np.asarray(f2).astype(np.int32).reshape(-1))
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
+    return ext, f1, f2, A, B
+
+
+def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 << 62,
+          trace: bool = True, labels: bool = False, snap_time: Optional[int] = None,
+          allow_timeout: bool = False) -> Result:
+    """O1: the paper's cycle loop.  Raises :class:`OracleError` on a non-OK status.
+
+    With ``allow_timeout`` a run stopped by ``max_cycles`` returns its work counts
+    (``cycles``, ``updates``, ``launched``) with ``F1 = -2`` instead of raising.
+    """
+    lib = _load()
+    ext, f1, f2, A, B = _common(extents, f1, f2, A, B)
+    V = int(np.prod(ext))
+    res = np.zeros(8, np.int64)
+    cap = 1 << 12
+    while True:
+        tr = np.zeros(3 * cap if trace else 3, np.int64)
+        tl = np.zeros(1, np.int64)
+        snap = np.zeros(V, np.int64) if snap_time is not None else None
+        sl = np.zeros(1, np.int64)
+        lab = np.zeros(V, np.int64) if labels else None
+        rc = lib.oracle_cycle(len(ext), _p64(ext), _p32(f1), _p32(f2), _p64(A), A.size, _p64(B), B.size,
+                              int(M), int(max_cycles), _p64(res), _p64(tr), cap if trace else 0, _p64(tl),
+                              -1 if snap_time is None else int(snap_time),
+                              _p64(snap) if snap is not None else None, _p64(sl),
+                              _p64(lab) if lab is not None else None)
+        if rc == TIMEOUT and allow_timeout:
+            res[:5] = -2
+        elif rc != OK:
+            raise OracleError(rc)
+        if not trace or tl[0] <= cap:
+            break
+        cap = int(tl[0])
+    return Result(*[int(x) for x in res[:8]],
+                  trace=tr[: 3 * int(tl[0])].reshape(-1, 3) if trace else None,
+                  labels=lab,
+                  snapshot=snap[: int(sl[0])] if snap is not None else None)
+
+
+def pareto(extents: Sequence[int], f1, f2, A, B, M: int) -> Result:
+    """O2: Dijkstra over (vertex, quality) states with dominance pruning."""
+    lib = _load()
+    ext, f1, f2, A, B = _common(extents, f1, f2, A, B)
+    res = np.zeros(8, np.int64)
+    rc = lib.oracle_pareto(len(ext), _p64(ext), _p32(f1), _p32(f2), _p64(A), A.size, _p64(B), B.size,
+                           int(M), _p64(res))
+    if rc != OK:
+        raise OracleError(rc)
+    r = Result(*[int(x) for x in res[:5]])
+    r.updates = int(res[6])
+    r.launched = int(res[7])
+    return r
+
+
+def lexmin(extents: Sequence[int], f1, f2, A, B):
+    """(F1, F2) of the lexicographically smallest walk from A to B, no weight bound."""
+    lib = _load()
+    ext, f1, f2, A, B = _common(extents, f1, f2, A, B)
+    res = np.zeros(2, np.int64)
+    rc = lib.oracle_lexmin(len(ext), _p64(ext), _p32(f1), _p32(f2), _p64(A), A.size, _p64(B), B.size,
+                           _p64(res))
+    if rc != OK:
+        raise OracleError(rc)
+    return int(res[0]), int(res[1])
+
+
+def solve_instance(inst, **kw) -> Result:
+    """O1 on a ``synth.Instance``-like object (anything with extents/f1/f2/A/B/M)."""
+    return cycle(inst.extents, inst.f1, inst.f2, inst.A, inst.B, inst.M, **kw)

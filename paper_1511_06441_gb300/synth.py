@@ -1,0 +1,303 @@
+"""Seeded synthetic inputs: lattices, weights, source/target sets and query streams.
+
+This module draws random numbers and lays them out; it contains none of the
+solver's arithmetic, so both the CUDA path and the CPU oracle can consume what it
+produces.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) used as a counter-based generator:
+value ``i`` of stream ``s`` under seed ``k`` is ``mix(base(k, s) + (i + 1) * GAMMA)``
+where ``mix`` is the SplitMix64 output function.  Every array has its own stream id,
+so arrays never share draws and any element can be regenerated independently.
+
+Lattice layout (shared by every consumer):
+
+* a vertex of the box ``[0, n_0) x ... x [0, n_{d-1})`` has the linear id
+  ``v = sum_k c_k * stride_k`` with coordinate 0 fastest;
+* ``f1[k, v]`` / ``f2[k, v]`` describe the edge ``(v, v + e_k)`` (travel time and
+  weight of Section 1 of the paper); entries on the upper face ``c_k = n_k - 1`` are
+  zero because that edge leaves the box;
+* ``f1 == 0`` marks an absent edge (a lattice subgraph).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# stream ids of the arrays drawn for one lattice / instance
+S_F1, S_F2, S_A, S_B, S_M, S_SHAPE, S_QUERY = 1, 2, 3, 4, 5, 6, 7
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.uint64, copy=True)
+    z ^= z >> np.uint64(30)
+    z *= _M1
+    z ^= z >> np.uint64(27)
+    z *= _M2
+    z ^= z >> np.uint64(31)
+    return z
+
+
+def u64(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """``n`` 64-bit draws of stream ``stream`` under ``seed``, starting at ``offset``."""
+    with np.errstate(over="ignore"):
+        key = _mix(np.array([(seed * 0x2545F4914F6CDD1D + stream) & (2**64 - 1)], dtype=np.uint64))[0]
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        return _mix(key + i * GAMMA)
+
+
+def uniform_int(seed: int, stream: int, n: int, lo: int, hi: int, offset: int = 0) -> np.ndarray:
+    """Integers in ``[lo, hi]`` as ``lo + x mod (hi - lo + 1)`` (int64)."""
+    span = np.uint64(hi - lo + 1)
+    return (u64(seed, stream, n, offset) % span).astype(np.int64) + lo
+
+
+def uniform_unit(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """Floats in ``[0, 1)`` from the top 53 bits."""
+    return (u64(seed, stream, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def geometric_clipped(seed: int, stream: int, n: int, p_num: int, p_den: int, cap: int) -> np.ndarray:
+    """Geometric(p = p_num/p_den) on {1, 2, ...}, clipped to ``cap``; inverse CDF in exact integers.
+
+    With ``u`` the top 53 bits of a draw, the value is ``1 + #{k >= 1 : u < 2^53 q^k}``
+    (``q = 1 - p``), i.e. P(value > k) = q^k.  The thresholds are exact rationals, so
+    the result does not depend on the platform's libm.
+    """
+    q_num = p_den - p_num
+    thr = [((1 << 53) * q_num ** k) // p_den ** k for k in range(1, cap)]
+    thr_arr = np.array(thr[::-1], dtype=np.int64)  # ascending
+    u = (u64(seed, stream, n) >> np.uint64(11)).astype(np.int64)
+    # count of thresholds strictly greater than u
+    greater = len(thr) - np.searchsorted(thr_arr, u, side="right")
+    return np.minimum(1 + greater, cap).astype(np.int64)
+
+
+# ---------------------------------------------------------------- lattice helpers
+
+def strides(extents: Sequence[int]) -> List[int]:
+    s, out = 1, []
+    for n in extents:
+        out.append(s)
+        s *= int(n)
+    return out
+
+
+def num_vertices(extents: Sequence[int]) -> int:
+    return int(np.prod([int(n) for n in extents], dtype=np.int64))
+
+
+def coords(v: np.ndarray, extents: Sequence[int]) -> np.ndarray:
+    """(len(v), d) coordinates of linear ids ``v``."""
+    v = np.asarray(v, dtype=np.int64)
+    out = np.empty((v.size, len(extents)), dtype=np.int64)
+    for k, n in enumerate(extents):
+        out[:, k] = v % n
+        v = v // n
+    return out
+
+
+def vertex_id(c: np.ndarray, extents: Sequence[int]) -> np.ndarray:
+    c = np.atleast_2d(np.asarray(c, dtype=np.int64))
+    st = np.array(strides(extents), dtype=np.int64)
+    return c @ st
+
+
+def face(extents: Sequence[int], k: int, c: int) -> np.ndarray:
+    """All vertex ids with coordinate ``k`` equal to ``c`` (ascending)."""
+    V = num_vertices(extents)
+    v = np.arange(V, dtype=np.int64)
+    st = strides(extents)
+    return v[(v // st[k]) % extents[k] == c]
+
+
+def upper_face_mask(extents: Sequence[int]) -> np.ndarray:
+    """(d, V) bool: True where edge (v, v+e_k) leaves the box."""
+    V = num_vertices(extents)
+    v = np.arange(V, dtype=np.int64)
+    st = strides(extents)
+    return np.stack([(v // st[k]) % extents[k] == extents[k] - 1 for k in range(len(extents))])
+
+
+@dataclasses.dataclass
+class Instance:
+    """One constrained-shortest-path problem on a box lattice (Section 1 of the paper)."""
+    extents: List[int]
+    f1: np.ndarray          # (d, V) uint8 | uint16
+    f2: np.ndarray          # (d, V) same dtype
+    A: np.ndarray           # int64 source vertex ids
+    B: np.ndarray           # int64 target vertex ids
+    M: int                  # weight bound, F2 < M
+    name: str = ""
+
+    @property
+    def d(self) -> int:
+        return len(self.extents)
+
+    @property
+    def V(self) -> int:
+        return num_vertices(self.extents)
+
+    @property
+    def weight_bytes(self) -> int:
+        return self.f1.dtype.itemsize
+
+
+def uniform_weights(extents: Sequence[int], lo: int, hi: int, seed: int,
+                    dtype=np.uint8, stream_base: int = 0):
+    """i.i.d. uniform integer travel times and weights in ``[lo, hi]``; upper faces zeroed."""
+    d, V = len(extents), num_vertices(extents)
+    f1 = uniform_int(seed, stream_base + S_F1, d * V, lo, hi).reshape(d, V)
+    f2 = uniform_int(seed, stream_base + S_F2, d * V, lo, hi).reshape(d, V)
+    up = upper_face_mask(extents)
+    f1[up] = 0
+    f2[up] = 0
+    return f1.astype(dtype), f2.astype(dtype)
+
+
+# ---------------------------------------------------------------- the workloads
+
+def workload_64x64(seed: int = 1) -> Instance:
+    """2-D 64x64, f1,f2 ~ U{1..10} uint8, A = column c0=0, B = column c0=63, M = 200."""
+    ext = [64, 64]
+    f1, f2 = uniform_weights(ext, 1, 10, seed)
+    return Instance(ext, f1, f2, face(ext, 0, 0), face(ext, 0, 63), 200, "lattice2d_64x64_M200")
+
+
+def workload_cube(side: int = 128, M: int = 1600, seed: int = 2) -> Instance:
+    """3-D cube side^3, f1,f2 ~ U{1..16} uint8, A = face c0=0, B = face c0=side-1."""
+    ext = [side, side, side]
+    f1, f2 = uniform_weights(ext, 1, 16, seed)
+    return Instance(ext, f1, f2, face(ext, 0, 0), face(ext, 0, side - 1), M,
+                    f"cube3d_{side}_M{M}")
+
+
+def anticorrelated_weights(extents: Sequence[int], seed: int = 3):
+    """f1 = min(255, Geometric(0.1)), f2 = 256 - f1, stored as uint16; upper faces zeroed."""
+    d, V = len(extents), num_vertices(extents)
+    f1 = geometric_clipped(seed, S_F1, d * V, 1, 10, 255).reshape(d, V)
+    f2 = 256 - f1
+    up = upper_face_mask(extents)
+    f1[up] = 0
+    f2[up] = 0
+    return f1.astype(np.uint16), f2.astype(np.uint16)
+
+
+def workload_anticorrelated(side: int = 4096, M: Optional[int] = None, seed: int = 3) -> Instance:
+    """2-D side x side with anti-correlated weights, A = corner 0, B = opposite corner.
+
+    ``M`` is 1.2 x the F2 of the lexicographic (F1, F2)-minimal unconstrained path; the
+    caller supplies it (it needs a shortest-path computation this module does not do).
+    """
+    ext = [side, side]
+    f1, f2 = anticorrelated_weights(ext, seed)
+    V = side * side
+    return Instance(ext, f1, f2, np.array([0], np.int64), np.array([V - 1], np.int64),
+                    int(M) if M is not None else 0, f"lattice2d_{side}_anticorr")
+
+
+def batch_instances(n: int = 512, seed: int = 4, side2d=(32, 1024), side3d=(16, 160)) -> List[Instance]:
+    """Mixed 2-D/3-D instances with log-uniform sides, U{1..32} weights, face-to-face A/B."""
+    out = []
+    for i in range(n):
+        sb = 16 * (i + 1)
+        r = uniform_unit(seed, sb + S_SHAPE, 5)
+        d = 2 if r[0] < 0.5 else 3
+        lo, hi = side2d if d == 2 else side3d
+        side = int(round(math.exp(math.log(lo) + r[1] * (math.log(hi) - math.log(lo)))))
+        ext = [side] * d
+        f1, f2 = uniform_weights(ext, 1, 32, seed, np.uint8, stream_base=sb)
+        k = min(int(r[2] * d), d - 1)
+        lowA = r[3] < 0.5
+        A = face(ext, k, 0 if lowA else side - 1)
+        B = face(ext, k, side - 1 if lowA else 0)
+        M = int(math.floor((0.5 + 1.5 * r[4]) * side * 16))
+        out.append(Instance(ext, f1, f2, A, B, M, f"batch{i}_d{d}_s{side}"))
+    return out
+
+
+def serving_lattice(side: int = 48, d: int = 4, seed: int = 5):
+    ext = [side] * d
+    f1, f2 = uniform_weights(ext, 1, 20, seed)
+    return ext, f1, f2
+
+
+@dataclasses.dataclass
+class Query:
+    A: np.ndarray
+    B: np.ndarray
+    M: int
+
+
+def serving_queries(n: int, extents: Sequence[int], seed: int = 5, start: int = 0) -> List[Query]:
+    """Queries with 1-64 distinct random sources, a random target hyperplane, M ~ U{200..2000}."""
+    d, V = len(extents), num_vertices(extents)
+    st = strides(extents)
+    out = []
+    for q in range(start, start + n):
+        sb = 1000 + 8 * q
+        hdr = uniform_int(seed, sb + S_QUERY, 4, 0, 2**31 - 1)
+        k = int(hdr[0] % d)
+        c = int(hdr[1] % extents[k])
+        nsrc = int(1 + hdr[2] % 64)
+        M = int(200 + hdr[3] % 1801)
+        B = face(extents, k, c)
+        chosen: List[int] = []
+        seen = set()
+        off = 0
+        while len(chosen) < nsrc:
+            cand = uniform_int(seed, sb + S_A, 64, 0, V - 1, offset=off)
+            off += 64
+            for v in cand.tolist():
+                if (v // st[k]) % extents[k] == c or v in seen:
+                    continue
+                seen.add(v)
+                chosen.append(v)
+                if len(chosen) == nsrc:
+                    break
+        out.append(Query(np.array(sorted(chosen), np.int64), B, M))
+    return out
+
+
+def random_small_instance(seed: int, max_vertices: int = 16, dims=(1, 2, 3), f_lo=(0, 1),
+                          f_hi: int = 6, absent_prob: float = 0.15) -> Instance:
+    """A tiny random lattice subgraph for brute-force comparisons.
+
+    Random dimension and extents with at most ``max_vertices`` vertices, travel times in
+    ``[1, f_hi]`` with some edges absent (f1 = 0), weights in ``[f2_lo, f_hi]`` with
+    ``f2_lo`` drawn from ``f_lo``, random disjoint A and B, M in ``[1, 25]``.
+    """
+    r = u64(seed, S_SHAPE, 16)
+    d = dims[int(r[0] % np.uint64(len(dims)))]
+    ext = [1] * d
+    # grow extents while the vertex budget allows
+    for i in range(1, 12):
+        k = int(r[i] % np.uint64(d))
+        if num_vertices(ext) // ext[k] * (ext[k] + 1) <= max_vertices:
+            ext[k] += 1
+    V = num_vertices(ext)
+    f1 = uniform_int(seed, S_F1, d * V, 1, f_hi).reshape(d, V)
+    f2lo = f_lo[int(r[12] % np.uint64(len(f_lo)))]
+    f2 = uniform_int(seed, S_F2, d * V, f2lo, f_hi).reshape(d, V)
+    absent = uniform_unit(seed, S_F1 + 100, d * V).reshape(d, V) < absent_prob
+    f1[absent] = 0
+    f2[absent] = 0
+    up = upper_face_mask(ext)
+    f1[up] = 0
+    f2[up] = 0
+    perm = np.argsort(u64(seed, S_A, V))
+    nA = 1 + int(r[13] % np.uint64(max(1, V // 3)))
+    nB = 1 + int(r[14] % np.uint64(max(1, (V - nA) // 2)))
+    nA = min(nA, V - 1)
+    nB = min(nB, V - nA)
+    A = np.sort(perm[:nA]).astype(np.int64)
+    B = np.sort(perm[nA:nA + nB]).astype(np.int64)
+    M = int(1 + r[15] % np.uint64(25))
+    return Instance(ext, f1.astype(np.uint8), f2.astype(np.uint8), A, B, M, f"tiny{seed}")

@@ -1,0 +1,143 @@
+/*
+ * csp.h - C ABI of libcsp, a CUDA (sm_103a) solver for the constrained shortest path
+ * problem on lattice graphs by the "water flow" cycle of I. Matic, "A parallel
+ * algorithm for the constrained shortest path problem on lattice graphs"
+ * (arXiv 1511.06441).
+ *
+ * Problem (Section 1 of the paper): an undirected lattice subgraph G of Z^d, every edge
+ * e with a travel time f1(e) >= 1 and a weight f2(e) >= 0 (integers), disjoint vertex
+ * sets A and B and a bound M.  Find F1 = min F1(pi) over paths pi from A to B with
+ * F2(pi) < M, plus the endpoint X in B, the last edge x = (Y -> X) and F2 of that path
+ * (what the paper's reconstruction by repeated application needs).
+ *
+ * Lattice layout (all entry points):
+ *   - d in [1, 4]; extents n_0..n_{d-1} >= 1; V = prod n_k < 2^28.
+ *   - vertex id v = sum_k c_k * stride_k, coordinate 0 fastest (stride_0 = 1).
+ *   - f1[k*V + v], f2[k*V + v] are travel time and weight of the edge (v, v + e_k),
+ *     stored as unsigned 8-bit or 16-bit integers (weight_bytes = 1 or 2).  Entries on
+ *     the upper face c_k = n_k - 1 are ignored.  f1 == 0 means the edge is absent.
+ *   - direction dir = 2k + s leads from a vertex to its neighbour v + e_k (s = 0) or
+ *     v - e_k (s = 1).
+ *
+ * Every call returns a csp_status and never aborts.  Pointers named *_dev are device
+ * pointers; all other pointers are host pointers.  Output buffers are owned by the
+ * caller.  Calls on the same lattice must not overlap (a lattice owns one workspace).
+ */
+#ifndef CSP_H
+#define CSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CSP_OK = 0,
+    CSP_ERR_INVALID = 1,  /* bad argument: d, extents, ids out of range, A and B not disjoint, empty A or B, M >= 2^31 */
+    CSP_ERR_OOM = 2,      /* device or host allocation failed */
+    CSP_ERR_CUDA = 3,     /* a CUDA call failed; csp_last_error() has the text */
+    CSP_ERR_CAPACITY = 4, /* the flow pool overflowed, or arrival times would reach 2^30 */
+    CSP_ERR_TIMEOUT = 5,  /* max_cycles reached */
+    CSP_ERR_BARRIER = 6   /* a device-side barrier wait gave up after its time limit */
+} csp_status;
+
+typedef struct csp_lattice csp_lattice;
+
+/* Result of one solve.  F1 = -1 (and X, x_src, x_dir, F2 = -1) when no path from A to
+ * B has F2 < M (termination 2 of the paper, Algorithm 2). */
+typedef struct {
+    int64_t F1;        /* minimal travel time F1(pi) subject to F2(pi) < M */
+    int64_t X;         /* endpoint in B: largest label (smallest F2), then smallest id */
+    int64_t x_src;     /* Y, the other end of the last edge x */
+    int64_t x_dir;     /* direction from Y to X (0 .. 2d-1) */
+    int64_t F2;        /* F2 of that path = M - Label(X) */
+    int64_t cycles;    /* cycles run = distinct times at which some label improved */
+    int64_t updates;   /* active-edge updates: sum over cycles of the flows alive at cycle start */
+    int64_t launched;  /* water flows started, phantoms included */
+    int64_t passes;    /* sweeps over the flow pool (cycles + prune-only passes) */
+    int64_t max_pool;  /* largest flow-pool size seen */
+    int64_t arrivals;  /* flows that delivered water (each improved its destination) */
+    int64_t improved;  /* label improvements = sum over cycles of the triggered vertices */
+} csp_result;
+
+typedef struct {
+    int64_t max_cycles;     /* stop with CSP_ERR_TIMEOUT after this many cycles; 0 = no limit */
+    int64_t pool_capacity;  /* flows per pool buffer; 0 = automatic.  csp_solve doubles it and
+                               retries on overflow; csp_solve_async reports CSP_ERR_CAPACITY */
+    int32_t ctas;           /* CTAs of the persistent kernel; 0 = chosen from the lattice size */
+    int32_t reserved;
+    void *stream;           /* cudaStream_t to run on; NULL = the legacy default stream */
+    void *ev_begin;         /* nullable cudaEvent_t recorded on the stream just before the cycle kernel */
+    void *ev_end;           /* nullable cudaEvent_t recorded just after it */
+} csp_options;
+
+/* Text for a status code (static storage). */
+const char *csp_status_string(csp_status s);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *csp_last_error(void);
+
+/* Creates a lattice: copies f1 and f2 (d*V entries each, layout above) into library-owned
+ * device memory and zeroes the ignored upper-face entries.  on_device = 1 means f1 and f2
+ * are device pointers.  stream: cudaStream_t or NULL.  *out receives the handle.
+ * Errors: CSP_ERR_INVALID (d, extents, weight_bytes), CSP_ERR_OOM, CSP_ERR_CUDA. */
+csp_status csp_create_lattice(int d, const int64_t *extents, const void *f1, const void *f2,
+                              int weight_bytes, int on_device, void *stream, csp_lattice **out);
+
+/* Overwrites the weights of an existing lattice (same layout and width as at creation),
+ * without allocating.  on_device as above. */
+csp_status csp_upload_weights(csp_lattice *lat, const void *f1, const void *f2, int on_device, void *stream);
+
+/* Frees the lattice and its workspace.  NULL is ignored. */
+void csp_destroy_lattice(csp_lattice *lat);
+
+/* Number of vertices of the lattice. */
+int64_t csp_num_vertices(const csp_lattice *lat);
+
+/* Allocates the solver workspace now (labels, offers, triggered list, two flow-pool
+ * buffers of pool_capacity flows; 0 = automatic), so that later solves allocate nothing. */
+csp_status csp_reserve(csp_lattice *lat, int64_t pool_capacity);
+
+/*
+ * Solves one instance: the cycle loop of Algorithm 1 (Initialization, Steps 1-9) run by
+ * one persistent GPU kernel until a vertex of B receives water (F1 found) or no flow is
+ * left (infeasible).
+ *   A, B       host arrays of vertex ids (duplicates allowed, treated as sets); nA, nB >= 1.
+ *   M          the bound, F2 < M; M <= 0 gives F1 = -1; M >= 2^31 is CSP_ERR_INVALID.
+ *   opt        nullable.
+ *   out        result (host).
+ *   trace      nullable host buffer of 3 * trace_cap int64: rows (Time, active vertices,
+ *              live flows) after the removals of each cycle, row 0 = after initialisation.
+ *              Requesting a trace makes the solve count active vertices (slower).
+ *   trace_len  nullable; receives the number of rows the solve produced.  If it exceeds
+ *              trace_cap only trace_cap rows were written (status still CSP_OK).
+ * Blocks the calling thread until the result is on the host.
+ */
+csp_status csp_solve(csp_lattice *lat, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB,
+                     int64_t M, const csp_options *opt, csp_result *out,
+                     int64_t *trace, int64_t trace_cap, int64_t *trace_len);
+
+/*
+ * Asynchronous solve with device-resident sets: enqueues the whole solve on opt->stream
+ * and returns without waiting.  A_dev, B_dev are device arrays of int64 ids.  The result
+ * is written to result_dev (device, 16 int64: status, F1, X, x_src, x_dir, F2, cycles,
+ * updates, launched, passes, max_pool, trace_len, (internal), arrivals, improved, 0).  Invalid ids, A and B not
+ * disjoint, pool overflow etc. are reported in result_dev[0], not by the return value
+ * (which reports only host-side argument errors and launch failures).  trace_dev:
+ * nullable device buffer of 3 * trace_cap int64.  The workspace must have been reserved
+ * (csp_reserve) with a capacity large enough for this instance.
+ */
+csp_status csp_solve_async(csp_lattice *lat, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB,
+                           int64_t M, const csp_options *opt, int64_t *result_dev,
+                           int64_t *trace_dev, int64_t trace_cap);
+
+/* Copies the labels left by the last solve (V int32: M - F2 of the best water that has
+ * reached each vertex by the final time, 0 if none) to labels_host. */
+csp_status csp_get_labels(csp_lattice *lat, int32_t *labels_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSP_H */

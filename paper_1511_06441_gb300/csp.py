@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libcsp (include/csp.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library; this module converts arrays and
+statuses and nothing else.  There is no CPU fallback: if ``libcsp.so`` is missing or
+cannot be loaded, :func:`lib` raises.
+
+Host arrays are numpy arrays.  Device arrays may be passed as torch CUDA tensors (torch
+is used only for device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcsp.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_BARRIER = range(7)
+RESULT_FIELDS = ("status", "F1", "X", "x_src", "x_dir", "F2", "cycles", "updates", "launched", "passes",
+                 "max_pool", "trace_len")
+
+_lib = None
+
+i64 = ctypes.c_int64
+i64p = ctypes.POINTER(ctypes.c_int64)
+vp = ctypes.c_void_p
+
+
+class CspResult(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("F1", "X", "x_src", "x_dir", "F2", "cycles", "updates", "launched", "passes", "max_pool",
+                 "arrivals", "improved")]
+
+
+class CspOptions(ctypes.Structure):
+    _fields_ = [("max_cycles", ctypes.c_int64), ("pool_capacity", ctypes.c_int64), ("ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stream", vp), ("ev_begin", vp), ("ev_end", vp)]
+
+
+class CspError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().csp_status_string(status).decode()
+        detail = lib().csp_last_error().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({detail})" if detail else ""))
+        self.status = status
+
+
+def lib():
+    """The loaded libcsp; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1511_06441_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.csp_status_string.restype = ctypes.c_char_p
+        L.csp_status_string.argtypes = [ctypes.c_int]
+        L.csp_last_error.restype = ctypes.c_char_p
+        L.csp_create_lattice.argtypes = [ctypes.c_int, i64p, vp, vp, ctypes.c_int, ctypes.c_int, vp,
+                                         ctypes.POINTER(vp)]
+        L.csp_upload_weights.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.csp_destroy_lattice.argtypes = [vp]
+        L.csp_destroy_lattice.restype = None
+        L.csp_num_vertices.argtypes = [vp]
+        L.csp_num_vertices.restype = i64
+        L.csp_reserve.argtypes = [vp, i64]
+        L.csp_solve.argtypes = [vp, i64p, i64, i64p, i64, i64, ctypes.POINTER(CspOptions),
+                                ctypes.POINTER(CspResult), i64p, i64, i64p]
+        L.csp_solve_async.argtypes = [vp, vp, i64, vp, i64, i64, ctypes.POINTER(CspOptions), vp, vp, i64]
+        L.csp_get_labels.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+        for f in ("csp_create_lattice", "csp_upload_weights", "csp_reserve", "csp_solve", "csp_solve_async",
+                  "csp_get_labels"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise CspError(status, where)
+
+
+def _ptr(a) -> int:
+    """Data pointer of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+@dataclasses.dataclass
+class Result:
+    F1: int
+    X: int
+    x_src: int
+    x_dir: int
+    F2: int
+    cycles: int
+    updates: int
+    launched: int
+    passes: int
+    max_pool: int
+    arrivals: int = -1
+    improved: int = -1
+    status: int = OK
+    trace: Optional[np.ndarray] = None
+
+    def answer(self):
+        return (self.F1, self.X, self.x_src, self.x_dir, self.F2)
+
+
+def _event_handle(ev) -> Optional[int]:
+    if ev is None:
+        return None
+    return getattr(ev, "cuda_event", ev)
+
+
+def options(max_cycles: int = 0, pool_capacity: int = 0, ctas: int = 0, stream=None,
+            ev_begin=None, ev_end=None) -> CspOptions:
+    return CspOptions(max_cycles, pool_capacity, ctas, 0, _stream_handle(stream), _event_handle(ev_begin),
+                      _event_handle(ev_end))
+
+
+class Lattice:
+    """A lattice resident on the GPU (``csp_create_lattice``)."""
+
+    def __init__(self, extents: Sequence[int], f1, f2, stream=None):
+        ext = np.ascontiguousarray(np.asarray(extents, dtype=np.int64))
+        on_device = not isinstance(f1, np.ndarray)
+        if on_device:
+            wb = f1.element_size()
+            if f1.dtype != f2.dtype or not (f1.is_contiguous() and f2.is_contiguous()):
+                raise ValueError("f1 and f2 must be contiguous and of the same dtype")
+        else:
+            f1 = np.ascontiguousarray(f1)
+            f2 = np.ascontiguousarray(f2)
+            if f1.dtype != f2.dtype or f1.dtype not in (np.uint8, np.uint16):
+                raise ValueError("f1 and f2 must both be uint8 or both uint16")
+            wb = f1.dtype.itemsize
+        self.extents = [int(x) for x in ext]
+        self.d = len(self.extents)
+        self.weight_bytes = wb
+        h = vp()
+        _check(lib().csp_create_lattice(self.d, ext.ctypes.data_as(i64p), _ptr(f1), _ptr(f2), wb, int(on_device),
+                                        _stream_handle(stream), ctypes.byref(h)), "csp_create_lattice")
+        self._h = h
+        self.V = int(lib().csp_num_vertices(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().csp_destroy_lattice(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload_weights(self, f1, f2, stream=None):
+        on_device = not isinstance(f1, np.ndarray)
+        _check(lib().csp_upload_weights(self._h, _ptr(f1), _ptr(f2), int(on_device), _stream_handle(stream)),
+               "csp_upload_weights")
+
+    def reserve(self, pool_capacity: int = 0):
+        _check(lib().csp_reserve(self._h, int(pool_capacity)), "csp_reserve")
+
+    def solve(self, A, B, M: int, *, trace: bool = False, trace_cap: int = 1 << 16, max_cycles: int = 0,
+              pool_capacity: int = 0, ctas: int = 0, stream=None, check: bool = True) -> Result:
+        """``csp_solve``: host sets in, host result out (blocks until done)."""
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
+        B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
+        opt = options(max_cycles, pool_capacity, ctas, stream)
+        res = CspResult()
+        tr = np.zeros(3 * trace_cap, np.int64) if trace else None
+        tl = ctypes.c_int64(0)
+        st = lib().csp_solve(self._h, A.ctypes.data_as(i64p), A.size, B.ctypes.data_as(i64p), B.size, int(M),
+                             ctypes.byref(opt), ctypes.byref(res),
+                             tr.ctypes.data_as(i64p) if tr is not None else None, trace_cap if trace else 0,
+                             ctypes.byref(tl))
+        if check:
+            _check(st, "csp_solve")
+        out = Result(*[int(getattr(res, name)) for name, _ in CspResult._fields_], status=st)
+        if tr is not None:
+            out.trace = tr[: 3 * min(int(tl.value), trace_cap)].reshape(-1, 3)
+            out.trace_len = int(tl.value)
+        return out
+
+    def solve_async(self, A_dev, B_dev, M: int, result_dev, *, trace_dev=None, trace_cap: int = 0,
+                    max_cycles: int = 0, ctas: int = 0, stream=None, ev_begin=None, ev_end=None):
+        """``csp_solve_async``: device sets (int64 tensors), device result (16 int64).
+
+        ``ev_begin``/``ev_end``: optional CUDA events recorded around the cycle kernel.
+        """
+        opt = options(max_cycles, 0, ctas, stream, ev_begin, ev_end)
+        _check(lib().csp_solve_async(self._h, _ptr(A_dev), int(A_dev.numel()), _ptr(B_dev), int(B_dev.numel()),
+                                     int(M), ctypes.byref(opt), _ptr(result_dev),
+                                     _ptr(trace_dev) if trace_dev is not None else None,
+                                     int(trace_cap)), "csp_solve_async")
+
+    def labels(self) -> np.ndarray:
+        out = np.zeros(self.V, np.int32)
+        _check(lib().csp_get_labels(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "csp_get_labels")
+        return out
+
+
+def result_from_record(rec) -> Result:
+    """Converts a 16-int64 result record (``csp_solve_async``) into a :class:`Result`."""
+    r = [int(x) for x in np.asarray(rec).reshape(-1)[:16]]
+    return Result(F1=r[1], X=r[2], x_src=r[3], x_dir=r[4], F2=r[5], cycles=r[6], updates=r[7], launched=r[8],
+                  passes=r[9], max_pool=r[10], arrivals=r[13], improved=r[14], status=r[0])
+
+
+def solve_instance(inst, **kw) -> Result:
+    """Creates a lattice for a ``synth.Instance`` and solves it once."""
+    lat = Lattice(inst.extents, inst.f1, inst.f2)
+    try:
+        return lat.solve(inst.A, inst.B, inst.M, **kw)
+    finally:
+        lat.close()

@@ -1,0 +1,715 @@
+// libcsp: the C ABI of include/csp.h and the persistent cycle kernel.
+//
+// One solve = a few set-up kernels (labels, B bitmap, sources) and ONE cooperative
+// persistent kernel that runs the whole cycle loop of Algorithm 1 on the device:
+//
+//   seed:  launch phase over A at Time 0 (Algorithm 3, Initialization)
+//   loop:  sweep the flow pool at the predicted time Tg        (Steps 1-3, 7-9)
+//          grid barrier
+//          launch phase over the vertices improved in the sweep (Steps 2, 4, 5, 8)
+//          grid barrier
+//          every CTA evaluates the same termination test        (Step 6, Algorithm 2)
+//
+// Tg is the smallest arrival time in the output pool, which may still hold flows that
+// died in the cycle just finished (they are removed by the next sweep, which checks
+// them against that cycle's labels).  If no live flow arrives at Tg, that sweep only
+// removes flows: it is not a cycle, nothing else changes, and the next sweep uses the
+// exact minimum.  Results and traces are therefore those of the cycle loop itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "csp.h"
+#include "csp_device.cuh"
+
+using namespace csp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+csp_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? CSP_ERR_OOM : CSP_ERR_CUDA;
+}
+
+#define CSP_CUDA(call)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+}  // namespace
+
+struct csp_lattice {
+    int d = 0;
+    int wbytes = 1;
+    int64_t ext[4] = {1, 1, 1, 1};
+    int stride[4] = {0, 0, 0, 0};
+    int64_t V = 0;
+    int device = 0;
+    void *f1 = nullptr, *f2 = nullptr;  // device [d][V]
+    unsigned long long flow_bound = 0;  // sum of f1 over directed edges: max flows alive
+    // workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t pool_cap = 0;
+    int32_t *label = nullptr;
+    unsigned long long *offer = nullptr;
+    uint32_t *isB = nullptr, *stamp = nullptr;
+    int32_t *trig = nullptr;
+    uint32_t *ed[2] = {nullptr, nullptr};
+    int32_t *qa[2] = {nullptr, nullptr}, *ta[2] = {nullptr, nullptr};
+    Control *ctl = nullptr;
+    long long *trace = nullptr;
+    int64_t trace_cap = 0;
+    int64_t *sets = nullptr;  // device copies of A and B
+    int64_t sets_cap = 0;
+};
+
+// ---------------------------------------------------------------- set-up kernels
+
+template <typename W>
+__global__ void k_zero_upper_faces(W *f1, W *f2, long long V, int d, long long s0, long long s1, long long s2,
+                                   long long s3, long long n0, long long n1, long long n2, long long n3)
+{
+    const long long st[4] = {s0, s1, s2, s3}, n[4] = {n0, n1, n2, n3};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d * V;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / V);
+        const long long v = i - k * V;
+        if ((v / st[k]) % n[k] == n[k] - 1) {
+            f1[i] = 0;
+            f2[i] = 0;
+        }
+    }
+}
+
+template <typename W>
+__global__ void k_flow_bound(const W *f1, long long n, unsigned long long *out)
+{
+    unsigned long long s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += f1[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, 2ull * s);
+}
+
+// Resets the control block for a new solve; clears the stamp array when the tag
+// counter is about to wrap.
+__global__ void k_reset(Control *ctl, uint32_t *stamp, long long V)
+{
+    const bool wrap = ctl->tag > 0xF0000000u || ctl->tag == 0u;
+    if (wrap)
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
+            stamp[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->bar = 0;
+        ctl->err = 0;
+        ctl->status_in = 0;
+        for (int b = 0; b < 2; b++) {
+            Counters &c = ctl->cnt[b];
+            c.n_live = c.launched = c.xkey = 0;
+            c.n_out = c.n_trig = c.arrivals = c.n_active = c.overflow = c.abort = 0;
+            c.min_ta = INT_MAX;
+        }
+        for (int i = 0; i < R_COUNT; i++) ctl->out[i] = 0;
+    }
+}
+
+__global__ void k_tag_fix(Control *ctl)
+{
+    if (ctl->tag > 0xF0000000u || ctl->tag == 0u) ctl->tag = 1;
+}
+
+// Marks B in the bitmap; out-of-range ids make the solve invalid.
+__global__ void k_mark_B(const int64_t *B, long long nB, uint32_t *isB, long long V, Control *ctl)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nB; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = B[i];
+        if (b < 0 || b >= V) atomicExch(&ctl->status_in, ST_INVALID);
+        else atomicOr(isB + (b >> 5), 1u << (b & 31));
+    }
+}
+
+// Initialization (Algorithm 3): Label(a) = M for a in A (the offer word mirrors it);
+// each distinct source is listed once as the "triggered" set of the seed launch.
+__global__ void k_mark_A(const int64_t *A, long long nA, const uint32_t *isB, long long V, int M, int32_t *label,
+                         unsigned long long *offer, int32_t *trig, Control *ctl)
+{
+    const unsigned long long key = ((unsigned long long)(uint32_t)M << 32) | 0xffffffffull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nA; i += (long long)gridDim.x * blockDim.x) {
+        const long long a = A[i];
+        if (a < 0 || a >= V) {
+            atomicExch(&ctl->status_in, ST_INVALID);
+            continue;
+        }
+        if ((isB[a >> 5] >> (a & 31)) & 1u) {
+            atomicExch(&ctl->status_in, ST_INVALID);  // A and B must be disjoint
+            continue;
+        }
+        label[a] = M;
+        if (atomicExch(offer + a, key) != key) trig[atomicAdd(&ctl->cnt[0].n_trig, 1u)] = (int32_t)a;
+    }
+}
+
+// ---------------------------------------------------------------- the persistent kernel
+
+template <typename W>
+__device__ void write_row(const Params<W> &P, long long row, long long time, long long active, long long flows)
+{
+    if (P.trace && row < P.trace_cap) {
+        P.trace[3 * row] = time;
+        P.trace[3 * row + 1] = active;
+        P.trace[3 * row + 2] = flows;
+    }
+}
+
+__device__ __forceinline__ void zero_counters(Counters *c)
+{
+    c->n_live = c->launched = c->xkey = 0;
+    c->n_out = c->n_trig = c->arrivals = c->n_active = c->overflow = c->abort = 0;
+    c->min_ta = INT_MAX;
+}
+
+__device__ __forceinline__ Counters read_counters(const Counters *c)
+{
+    Counters r;
+    const volatile Counters *vc = c;
+    r.n_live = vc->n_live;
+    r.launched = vc->launched;
+    r.xkey = vc->xkey;
+    r.n_out = vc->n_out;
+    r.n_trig = vc->n_trig;
+    r.arrivals = vc->arrivals;
+    r.n_active = vc->n_active;
+    r.overflow = vc->overflow;
+    r.min_ta = vc->min_ta;
+    r.abort = vc->abort;
+    return r;
+}
+
+template <int D, typename W, bool TRACE>
+__global__ void __launch_bounds__(TPB, 2) k_cycle(Params<W> P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileStage &stage = *reinterpret_cast<TileStage *>(smem_raw);
+    __shared__ uint32_t s_warp[NWARP];
+    __shared__ uint32_t s_base[2];
+
+    Control *ctl = P.ctl;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long epoch = 0;
+    const int M = P.M;
+    const unsigned int tag0 = *(volatile unsigned int *)&ctl->tag;
+    const unsigned long long t_start = globaltimer_ns();
+
+    long long cycle = 0, updates = 0, launched = 0, passes = 0, trace_len = 0, arrivals = 0, improved = 0;
+    unsigned int max_pool = 0;
+    int Time = 0, status = ST_OK;
+    bool feasible = false;
+    unsigned long long xkey = 0;
+    int last_buf = 0;
+
+    if (*(volatile int *)&ctl->status_in != 0) {
+        status = *(volatile int *)&ctl->status_in;
+        goto finish;
+    }
+    if (M <= 0) {  // no walk has F2 < M <= 0
+        trace_len = 1;
+        if (leader) write_row(P, 0, 0, 0, 0);
+        goto finish;
+    }
+
+    {
+        // seed: water leaves A at Time 0 along every edge that can raise a label
+        LocalStats st{0, 0, 0, 0, INT_MAX};
+        const uint32_t n_seed = min(*(volatile unsigned int *)&ctl->cnt[0].n_trig, P.trig_cap);
+        launch<D, W>(P, 0, n_seed, 0, &ctl->cnt[0], st, stage, s_warp, s_base);
+        flush_stats(st, &ctl->cnt[0]);
+        if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
+        const Counters c = read_counters(&ctl->cnt[0]);
+        launched += (long long)c.launched;
+        if (c.overflow) { status = ST_CAPACITY; goto finish; }
+        if (c.n_out == 0) {  // nothing can leave A: infeasible
+            if (leader) write_row(P, 0, 0, 0, 0);
+            trace_len = 1;
+            goto finish;
+        }
+        max_pool = c.n_out;
+        int Tg = c.min_ta;
+
+        for (long long pass = 1;; pass++) {
+            const int ib = (int)((pass - 1) & 1), ob = ib ^ 1;
+            Counters *C = &ctl->cnt[ob];
+            const uint32_t n_in = *(volatile unsigned int *)&ctl->cnt[ib].n_out;
+            LocalStats sa{0, 0, 0, 0, INT_MAX};
+            sweep<D, W, TRACE>(P, ib, n_in, Tg, C, tag0 + (uint32_t)pass, sa, stage, s_warp, s_base);
+            flush_stats(sa, C);
+            if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
+            if (leader) zero_counters(&ctl->cnt[ib]);  // everyone has read n_in
+            if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
+            LocalStats sb{0, 0, 0, 0, INT_MAX};
+            const uint32_t n_trig = min(*(volatile unsigned int *)&C->n_trig, P.trig_cap);
+            launch<D, W>(P, ob, n_trig, Tg, C, sb, stage, s_warp, s_base);
+            flush_stats(sb, C);
+            if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
+            passes = pass;
+            last_buf = ob;
+
+            const Counters c = read_counters(C);
+            launched += (long long)c.launched;
+            arrivals += (long long)c.arrivals;
+            improved += (long long)c.n_trig;
+            if (c.overflow) { status = ST_CAPACITY; goto finish; }
+            if (c.abort) { status = ST_TIMEOUT; goto finish; }
+            if (c.arrivals > 0) {  // a real cycle at time Tg
+                if (TRACE && leader) write_row(P, cycle, Time, c.n_active, (long long)c.n_live);
+                updates += (long long)c.n_live;
+                cycle++;
+                Time = Tg;
+                if (c.xkey) {  // a vertex of B improved: F1 = Time (Algorithm 2)
+                    feasible = true;
+                    xkey = c.xkey;
+                    if (TRACE) {
+                        // the terminal cycle's row: count the flows still alive after it
+                        LocalStats sc{0, 0, 0, 0, INT_MAX};
+                        sweep<D, W, TRACE>(P, ob, c.n_out, -1, &ctl->cnt[ib], tag0 + (uint32_t)pass + 1u, sc, stage,
+                                           s_warp, s_base);
+                        flush_stats(sc, &ctl->cnt[ib]);
+                        if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
+                        const Counters cc = read_counters(&ctl->cnt[ib]);
+                        if (leader) write_row(P, cycle, Time, cc.n_active, (long long)cc.n_live);
+                        trace_len = cycle + 1;
+                    }
+                    goto finish;
+                }
+            } else if (c.n_live == 0) {  // the pool held no live flow: infeasible
+                if (TRACE && leader) write_row(P, cycle, Time, 0, 0);
+                trace_len = cycle + 1;
+                goto finish;
+            }
+            if (c.n_out == 0) {  // no flow left after a cycle: infeasible
+                if (TRACE && leader) write_row(P, cycle, Time, 0, 0);
+                trace_len = cycle + 1;
+                goto finish;
+            }
+            max_pool = max(max_pool, c.n_out);
+            Tg = c.min_ta;
+            if (P.max_cycles > 0 && cycle >= P.max_cycles) { status = ST_TIMEOUT; goto finish; }
+            if (Tg >= TIME_LIMIT) { status = ST_CAPACITY; goto finish; }
+        }
+    }
+
+finish:
+    if (leader) {
+        long long *o = ctl->out;
+        for (int i = 0; i < R_COUNT; i++) o[i] = -1;
+        o[R_STATUS] = status;
+        if (status == ST_OK && feasible) {
+            const uint32_t X = 0xffffffffu - (uint32_t)(xkey & 0xffffffffu);
+            const int LX = (int)(xkey >> 32);
+            const uint32_t code = 0xffffffffu - (uint32_t)(__ldcg(P.offer + X) & 0xffffffffu);
+            o[R_F1] = Time;
+            o[R_X] = X;
+            o[R_XSRC] = code >> 3;
+            o[R_XDIR] = code & 7u;
+            o[R_F2] = (long long)M - LX;
+        }
+        o[R_CYCLES] = cycle;
+        o[R_UPDATES] = updates;
+        o[R_LAUNCHED] = launched;
+        o[R_PASSES] = passes;
+        o[R_MAXPOOL] = max_pool;
+        o[R_TRACELEN] = TRACE ? trace_len : 0;
+        o[R_NEXTTAG] = tag0 + passes + 2;
+        o[R_ARRIVALS] = arrivals;
+        o[R_IMPROVED] = improved;
+        ctl->tag = tag0 + (uint32_t)passes + 2u;
+        if (P.result_dev)
+            for (int i = 0; i < R_COUNT; i++) P.result_dev[i] = o[i];
+    }
+    (void)last_buf;
+}
+
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+template <int D, typename W, bool TRACE>
+const void *kernel_ptr()
+{
+    return (const void *)&k_cycle<D, W, TRACE>;
+}
+
+template <typename W, bool TRACE>
+const void *pick_kernel_w(int d)
+{
+    switch (d) {
+    case 1: return kernel_ptr<1, W, TRACE>();
+    case 2: return kernel_ptr<2, W, TRACE>();
+    case 3: return kernel_ptr<3, W, TRACE>();
+    default: return kernel_ptr<4, W, TRACE>();
+    }
+}
+
+const void *pick_kernel(int d, int wbytes, bool trace)
+{
+    if (wbytes == 1) return trace ? pick_kernel_w<uint8_t, true>(d) : pick_kernel_w<uint8_t, false>(d);
+    return trace ? pick_kernel_w<uint16_t, true>(d) : pick_kernel_w<uint16_t, false>(d);
+}
+
+constexpr size_t kSmem = sizeof(TileStage);
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
+{
+    if (L->ws && pool_cap <= L->pool_cap && sets_cap <= L->sets_cap) return CSP_OK;
+    pool_cap = std::max<int64_t>(pool_cap, L->pool_cap);
+    sets_cap = std::max<int64_t>(sets_cap, L->sets_cap);
+    if (pool_cap > 0xF0000000ll) pool_cap = 0xF0000000ll;
+    const int64_t V = L->V;
+    const int64_t trace_cap = L->trace_cap ? L->trace_cap : 1 << 16;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
+                 o_stamp = take(V * 4), o_trig = take(V * 4), o_ctl = take(sizeof(Control)),
+                 o_trace = take(trace_cap * 24), o_sets = take(sets_cap * 8);
+    size_t o_pool[2][3];
+    for (int b = 0; b < 2; b++)
+        for (int f = 0; f < 3; f++) o_pool[b][f] = take(pool_cap * 4);
+    void *ws = nullptr;
+    cudaError_t e = cudaMalloc(&ws, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    if (L->ws) cudaFree(L->ws);
+    L->ws = ws;
+    L->ws_bytes = off;
+    char *b = (char *)ws;
+    L->label = (int32_t *)(b + o_label);
+    L->offer = (unsigned long long *)(b + o_offer);
+    L->isB = (uint32_t *)(b + o_isB);
+    L->stamp = (uint32_t *)(b + o_stamp);
+    L->trig = (int32_t *)(b + o_trig);
+    L->ctl = (Control *)(b + o_ctl);
+    L->trace = (long long *)(b + o_trace);
+    L->trace_cap = trace_cap;
+    L->sets = (int64_t *)(b + o_sets);
+    L->sets_cap = sets_cap;
+    for (int k = 0; k < 2; k++) {
+        L->ed[k] = (uint32_t *)(b + o_pool[k][0]);
+        L->qa[k] = (int32_t *)(b + o_pool[k][1]);
+        L->ta[k] = (int32_t *)(b + o_pool[k][2]);
+    }
+    L->pool_cap = pool_cap;
+    CSP_CUDA(cudaMemset(L->stamp, 0, V * 4));
+    CSP_CUDA(cudaMemset(L->ctl, 0, sizeof(Control)));
+    return CSP_OK;
+}
+
+int64_t default_pool_cap(const csp_lattice *L)
+{
+    const int64_t want = std::max<int64_t>(1 << 20, 16 * L->V);
+    return (int64_t)std::min<unsigned long long>((unsigned long long)want, std::max(L->flow_bound, 1024ull));
+}
+
+int num_sms(int device)
+{
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+    return n > 0 ? n : 1;
+}
+
+// Enqueues one solve (set-up kernels + persistent kernel) on stream s.
+csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB, int64_t M,
+                         const csp_options *opt, long long *trace_dev, int64_t trace_cap, int64_t *result_dev,
+                         cudaStream_t s)
+{
+    const int64_t V = L->V;
+    CSP_CUDA(cudaMemsetAsync(L->label, 0, V * 4, s));
+    CSP_CUDA(cudaMemsetAsync(L->offer, 0, V * 8, s));
+    CSP_CUDA(cudaMemsetAsync(L->isB, 0, ((V + 31) / 32) * 4, s));
+    const int sms = num_sms(L->device);
+    k_reset<<<sms, 256, 0, s>>>(L->ctl, L->stamp, V);
+    k_tag_fix<<<1, 1, 0, s>>>(L->ctl);
+    k_mark_B<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nB + 255) / 256)), 256, 0, s>>>(B_dev, nB, L->isB, V,
+                                                                                                 L->ctl);
+    k_mark_A<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nA + 255) / 256)), 256, 0, s>>>(
+        A_dev, nA, L->isB, V, (int)M, L->label, L->offer, L->trig, L->ctl);
+    CSP_CUDA(cudaGetLastError());
+
+    const bool trace = trace_dev != nullptr;
+    const void *fn = pick_kernel(L->d, L->wbytes, trace);
+    static thread_local bool attr_set[2][2][5] = {};
+    bool &done = attr_set[L->wbytes - 1][trace][L->d];
+    if (!done) {
+        CSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+        done = true;
+    }
+    int per_sm = 0;
+    CSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TPB, kSmem));
+    if (per_sm < 1) {
+        g_last_error = "persistent kernel does not fit on an SM";
+        return CSP_ERR_CUDA;
+    }
+    const int max_ctas = per_sm * sms;
+    int ctas = opt && opt->ctas > 0 ? opt->ctas : (int)std::min<int64_t>(max_ctas, std::max<int64_t>(1, V / 4096));
+    ctas = std::max(1, std::min(ctas, max_ctas));
+
+    Params<uint8_t> P8{};
+    Params<uint16_t> P16{};
+    auto fill = [&](auto &P) {
+        using W = std::remove_cv_t<std::remove_pointer_t<decltype(P.f1)>>;
+        P.f1 = (const W *)L->f1;
+        P.f2 = (const W *)L->f2;
+        P.V = V;
+        for (int k = 0; k < 4; k++) P.stride[k] = L->stride[k];
+        P.label = L->label;
+        P.offer = L->offer;
+        P.isB = L->isB;
+        P.stamp = L->stamp;
+        P.trig = L->trig;
+        P.trig_cap = (unsigned int)V;
+        for (int b = 0; b < 2; b++) {
+            P.ed[b] = L->ed[b];
+            P.qa[b] = L->qa[b];
+            P.ta[b] = L->ta[b];
+        }
+        P.pool_cap = (unsigned int)L->pool_cap;
+        P.ctl = L->ctl;
+        P.trace = trace_dev;
+        P.trace_cap = trace_cap;
+        P.result_dev = (long long *)result_dev;
+        P.M = (int)M;
+        P.max_cycles = opt ? opt->max_cycles : 0;
+        P.budget_ns = 120ull * 1000000000ull;  // no single solve is expected to take minutes
+    };
+    void *args[1];
+    if (L->wbytes == 1) {
+        fill(P8);
+        args[0] = &P8;
+    } else {
+        fill(P16);
+        args[0] = &P16;
+    }
+    if (opt && opt->ev_begin) CSP_CUDA(cudaEventRecord((cudaEvent_t)opt->ev_begin, s));
+    CSP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(TPB), args, kSmem, s));
+    if (opt && opt->ev_end) CSP_CUDA(cudaEventRecord((cudaEvent_t)opt->ev_end, s));
+    return CSP_OK;
+}
+
+csp_status check_sets_host(const csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB)
+{
+    if (!A || !B || nA < 1 || nB < 1) return CSP_ERR_INVALID;
+    std::vector<int64_t> a(A, A + nA), b(B, B + nB);
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    if (a.front() < 0 || a.back() >= L->V || b.front() < 0 || b.back() >= L->V) return CSP_ERR_INVALID;
+    size_t i = 0, j = 0;
+    while (i < a.size() && j < b.size()) {
+        if (a[i] == b[j]) return CSP_ERR_INVALID;  // A and B must be disjoint
+        if (a[i] < b[j]) i++;
+        else j++;
+    }
+    return CSP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char *csp_status_string(csp_status s)
+{
+    switch (s) {
+    case CSP_OK: return "ok";
+    case CSP_ERR_INVALID: return "invalid argument";
+    case CSP_ERR_OOM: return "out of memory";
+    case CSP_ERR_CUDA: return "CUDA error";
+    case CSP_ERR_CAPACITY: return "flow pool capacity exceeded";
+    case CSP_ERR_TIMEOUT: return "cycle limit reached";
+    case CSP_ERR_BARRIER: return "device barrier timed out";
+    }
+    return "unknown status";
+}
+
+const char *csp_last_error(void) { return g_last_error.c_str(); }
+
+csp_status csp_create_lattice(int d, const int64_t *extents, const void *f1, const void *f2, int weight_bytes,
+                              int on_device, void *stream, csp_lattice **out)
+{
+    if (!out || !extents || !f1 || !f2 || d < 1 || d > 4 || (weight_bytes != 1 && weight_bytes != 2))
+        return CSP_ERR_INVALID;
+    *out = nullptr;
+    int64_t V = 1;
+    for (int k = 0; k < d; k++) {
+        if (extents[k] < 1 || extents[k] >= (1ll << 28)) return CSP_ERR_INVALID;
+        V *= extents[k];
+        if (V >= (1ll << 28)) return CSP_ERR_INVALID;
+    }
+    csp_lattice *L = new (std::nothrow) csp_lattice();
+    if (!L) return CSP_ERR_OOM;
+    L->d = d;
+    L->wbytes = weight_bytes;
+    L->V = V;
+    int64_t s = 1;
+    for (int k = 0; k < d; k++) {
+        L->ext[k] = extents[k];
+        L->stride[k] = (int)s;
+        s *= extents[k];
+    }
+    cudaGetDevice(&L->device);
+    const size_t bytes = (size_t)d * V * weight_bytes;
+    cudaError_t e = cudaMalloc(&L->f1, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&L->f2, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        csp_destroy_lattice(L);
+        return cuda_fail(e, "cudaMalloc(lattice)");
+    }
+    csp_status st = csp_upload_weights(L, f1, f2, on_device, stream);
+    if (st != CSP_OK) {
+        csp_destroy_lattice(L);
+        return st;
+    }
+    *out = L;
+    return CSP_OK;
+}
+
+csp_status csp_upload_weights(csp_lattice *L, const void *f1, const void *f2, int on_device, void *stream)
+{
+    if (!L || !f1 || !f2) return CSP_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)L->d * L->V * L->wbytes;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CSP_CUDA(cudaMemcpyAsync(L->f1, f1, bytes, kind, s));
+    CSP_CUDA(cudaMemcpyAsync(L->f2, f2, bytes, kind, s));
+    const long long n[4] = {L->ext[0], L->ext[1], L->ext[2], L->ext[3]};
+    const long long st[4] = {L->stride[0], L->stride[1], L->stride[2], L->stride[3]};
+    const int blocks = std::max<int64_t>(1, std::min<int64_t>(4096, (L->d * L->V + 255) / 256));
+    unsigned long long *bound = nullptr;
+    CSP_CUDA(cudaMallocAsync((void **)&bound, sizeof(unsigned long long), s));
+    CSP_CUDA(cudaMemsetAsync(bound, 0, sizeof(unsigned long long), s));
+    if (L->wbytes == 1) {
+        k_zero_upper_faces<uint8_t><<<blocks, 256, 0, s>>>((uint8_t *)L->f1, (uint8_t *)L->f2, L->V, L->d, st[0], st[1],
+                                                           st[2], st[3], n[0], n[1], n[2], n[3]);
+        k_flow_bound<uint8_t><<<blocks, 256, 0, s>>>((const uint8_t *)L->f1, L->d * L->V, bound);
+    } else {
+        k_zero_upper_faces<uint16_t><<<blocks, 256, 0, s>>>((uint16_t *)L->f1, (uint16_t *)L->f2, L->V, L->d, st[0],
+                                                            st[1], st[2], st[3], n[0], n[1], n[2], n[3]);
+        k_flow_bound<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t *)L->f1, L->d * L->V, bound);
+    }
+    CSP_CUDA(cudaGetLastError());
+    CSP_CUDA(cudaMemcpyAsync(&L->flow_bound, bound, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CSP_CUDA(cudaFreeAsync(bound, s));
+    CSP_CUDA(cudaStreamSynchronize(s));
+    return CSP_OK;
+}
+
+void csp_destroy_lattice(csp_lattice *L)
+{
+    if (!L) return;
+    if (L->f1) cudaFree(L->f1);
+    if (L->f2) cudaFree(L->f2);
+    if (L->ws) cudaFree(L->ws);
+    delete L;
+}
+
+int64_t csp_num_vertices(const csp_lattice *L) { return L ? L->V : -1; }
+
+csp_status csp_reserve(csp_lattice *L, int64_t pool_capacity)
+{
+    if (!L || pool_capacity < 0) return CSP_ERR_INVALID;
+    return ensure_workspace(L, pool_capacity ? pool_capacity : default_pool_cap(L), std::max<int64_t>(L->sets_cap, 1024));
+}
+
+csp_status csp_solve_async(csp_lattice *L, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB,
+                           int64_t M, const csp_options *opt, int64_t *result_dev, int64_t *trace_dev, int64_t trace_cap)
+{
+    if (!L || !A_dev || !B_dev || nA < 1 || nB < 1 || !result_dev || M >= (1ll << 31) || M < -(1ll << 31) + 1)
+        return CSP_ERR_INVALID;
+    if (trace_dev && trace_cap < 1) return CSP_ERR_INVALID;
+    if (!L->ws) return CSP_ERR_INVALID;  // csp_reserve first
+    cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
+    return enqueue_solve(L, A_dev, nA, B_dev, nB, M, opt, (long long *)trace_dev, trace_dev ? trace_cap : 0, result_dev,
+                         s);
+}
+
+csp_status csp_solve(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                     const csp_options *opt, csp_result *out, int64_t *trace, int64_t trace_cap, int64_t *trace_len)
+{
+    if (!L || !out || M >= (1ll << 31) || M < -(1ll << 31) + 1) return CSP_ERR_INVALID;
+    if (trace && trace_cap < 0) return CSP_ERR_INVALID;
+    csp_status st = check_sets_host(L, A, nA, B, nB);
+    if (st != CSP_OK) return st;
+    cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
+    int64_t cap = opt && opt->pool_capacity > 0 ? opt->pool_capacity : std::max<int64_t>(L->pool_cap, default_pool_cap(L));
+    if (trace && trace_cap > L->trace_cap) {
+        L->trace_cap = trace_cap;
+        if (L->ws) {  // grow the device trace buffer with the workspace
+            cudaFree(L->ws);
+            L->ws = nullptr;
+            L->pool_cap = 0;
+            L->sets_cap = 0;
+        }
+    }
+    for (int attempt = 0;; attempt++) {
+        st = ensure_workspace(L, cap, nA + nB);
+        if (st != CSP_OK) return st;
+        CSP_CUDA(cudaMemcpyAsync(L->sets, A, nA * 8, cudaMemcpyHostToDevice, s));
+        CSP_CUDA(cudaMemcpyAsync(L->sets + nA, B, nB * 8, cudaMemcpyHostToDevice, s));
+        st = enqueue_solve(L, L->sets, nA, L->sets + nA, nB, M, opt, trace ? L->trace : nullptr,
+                           trace ? L->trace_cap : 0, nullptr, s);
+        if (st != CSP_OK) return st;
+        long long o[R_COUNT];
+        CSP_CUDA(cudaMemcpyAsync(o, (char *)L->ctl + offsetof(Control, out), sizeof(o), cudaMemcpyDeviceToHost, s));
+        CSP_CUDA(cudaStreamSynchronize(s));
+        if (o[R_STATUS] == ST_CAPACITY && L->pool_cap < (int64_t)L->flow_bound && L->pool_cap < 0xF0000000ll) {
+            cap = std::min<int64_t>(2 * L->pool_cap, (int64_t)std::max(L->flow_bound, 1024ull));
+            continue;  // grow the pool and run again
+        }
+        out->F1 = o[R_F1];
+        out->X = o[R_X];
+        out->x_src = o[R_XSRC];
+        out->x_dir = o[R_XDIR];
+        out->F2 = o[R_F2];
+        out->cycles = o[R_CYCLES];
+        out->updates = o[R_UPDATES];
+        out->launched = o[R_LAUNCHED];
+        out->passes = o[R_PASSES];
+        out->max_pool = o[R_MAXPOOL];
+        out->arrivals = o[R_ARRIVALS];
+        out->improved = o[R_IMPROVED];
+        if (trace) {
+            const int64_t rows = std::min<int64_t>(o[R_TRACELEN], trace_cap);
+            if (rows > 0) CSP_CUDA(cudaMemcpy(trace, L->trace, rows * 24, cudaMemcpyDeviceToHost));
+        }
+        if (trace_len) *trace_len = trace ? o[R_TRACELEN] : 0;
+        return (csp_status)o[R_STATUS];
+    }
+}
+
+csp_status csp_get_labels(csp_lattice *L, int32_t *labels_host)
+{
+    if (!L || !labels_host || !L->ws) return CSP_ERR_INVALID;
+    CSP_CUDA(cudaMemcpy(labels_host, L->label, L->V * 4, cudaMemcpyDeviceToHost));
+    return CSP_OK;
+}
+
+}  // extern "C"

@@ -132,6 +132,37 @@ csp_status csp_solve_async(csp_lattice *lat, const int64_t *A_dev, int64_t nA, c
                            int64_t M, const csp_options *opt, int64_t *result_dev,
                            int64_t *trace_dev, int64_t trace_cap);
 
+/*
+ * Solve without any device allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc (for example code running inside a
+ * framework or runtime that owns every device allocation, or under a memory cap that
+ * forbids new allocations).  The solver's scratch memory lives in one file-scope device
+ * array of CSP_STATIC_WORKSPACE_BYTES bytes that every GPU loading this library holds
+ * until the library is unloaded.
+ *   extents, d       as for csp_create_lattice (host array).
+ *   f1_dev, f2_dev   the caller's device weights, layout as above; here the upper-face
+ *                    entries of f1 MUST be zero (a nonzero one is reported as
+ *                    CSP_ERR_INVALID in result_dev[0]).
+ *   A_dev, B_dev     device arrays of int64 vertex ids (sets, as for csp_solve_async).
+ *   M, max_cycles    as for csp_solve (max_cycles 0 = no limit).
+ *   stream           cudaStream_t or NULL.
+ *   result_dev       device record of 16 int64, laid out as for csp_solve_async.
+ * Enqueues the solve and returns without waiting.  The layout needs 16.2 bytes per vertex
+ * plus 24 bytes per flow-pool slot (two buffers); whatever the vertex arrays leave of the
+ * static array becomes the flow pool.  A lattice whose vertex arrays do not fit is
+ * rejected with CSP_ERR_INVALID (csp_last_error() says so); a solve whose flows do not fit
+ * reports CSP_ERR_CAPACITY in result_dev[0].  No trace is recorded.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) for that device;
+ * make that first call before capturing any stream.  All calls share the array and
+ * each call overwrites what the previous one left, so calls that may overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ */
+#define CSP_STATIC_WORKSPACE_BYTES (64u << 20)
+
+csp_status csp_solve_static(int d, const int64_t *extents, const void *f1_dev, const void *f2_dev,
+                            int weight_bytes, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB,
+                            int64_t M, int64_t max_cycles, void *stream, int64_t *result_dev);
+
 /* Copies the labels left by the last solve (V int32: M - F2 of the best water that has
  * reached each vertex by the final time, 0 if none) to labels_host. */
 csp_status csp_get_labels(csp_lattice *lat, int32_t *labels_host);

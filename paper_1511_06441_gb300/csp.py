@@ -71,8 +71,9 @@ def lib():
                                 ctypes.POINTER(CspResult), i64p, i64, i64p]
         L.csp_solve_async.argtypes = [vp, vp, i64, vp, i64, i64, ctypes.POINTER(CspOptions), vp, vp, i64]
         L.csp_get_labels.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+        L.csp_solve_static.argtypes = [ctypes.c_int, i64p, vp, vp, ctypes.c_int, vp, i64, vp, i64, i64, i64, vp, vp]
         for f in ("csp_create_lattice", "csp_upload_weights", "csp_reserve", "csp_solve", "csp_solve_async",
-                  "csp_get_labels"):
+                  "csp_get_labels", "csp_solve_static"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -230,3 +231,17 @@ def solve_instance(inst, **kw) -> Result:
         return lat.solve(inst.A, inst.B, inst.M, **kw)
     finally:
         lat.close()
+
+
+def solve_static(extents, f1_dev, f2_dev, A_dev, B_dev, M: int, result_dev, *, max_cycles: int = 0, stream=None):
+    """``csp_solve_static``: solve with no device allocation (scratch in the library's static array).
+
+    For callers that cannot allocate device memory.  Weights and sets are the caller's
+    device tensors (upper-face travel times must be zero); the 16-int64 result record is
+    written to ``result_dev``.  Returns after enqueueing; synchronise the stream to read it.
+    """
+    ext = np.ascontiguousarray(np.asarray(extents, dtype=np.int64))
+    _check(lib().csp_solve_static(len(ext), ext.ctypes.data_as(i64p), _ptr(f1_dev), _ptr(f2_dev),
+                                  f1_dev.element_size(), _ptr(A_dev), int(A_dev.numel()), _ptr(B_dev),
+                                  int(B_dev.numel()), int(M), int(max_cycles), _stream_handle(stream),
+                                  _ptr(result_dev)), "csp_solve_static")

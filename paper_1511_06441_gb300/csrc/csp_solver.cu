@@ -713,3 +713,179 @@ csp_status csp_get_labels(csp_lattice *L, int32_t *labels_host)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- solve without allocation
+//
+// For callers that cannot allocate device memory (code running where cudaMalloc is not
+// allowed, such as inside a memory-capped host process or a framework that owns all
+// allocations).  The solver's scratch lives in one file-scope device array instead of a
+// per-lattice workspace.  The array exists on every GPU that loads this library, for as
+// long as the library stays loaded.  All calls share it, so calls whose work overlaps on
+// the GPU (on different streams, or from different threads) race; a call clears what must
+// start at zero (labels, offers, the B bitmap and the control block) before it starts.
+
+namespace {
+
+constexpr size_t kStaticBytes = (size_t)CSP_STATIC_WORKSPACE_BYTES;
+static __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_static_addr[kMaxDevices] = {};
+
+// Host code cannot use g_static_ws directly: on the host that name is only a stand-in.
+// The device address is looked up once per device, with that device current.
+csp_status static_workspace_address(void **out)
+{
+    int dev = 0;
+    CSP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        g_last_error = "csp_solve_static: device index out of range";
+        return CSP_ERR_INVALID;
+    }
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        CSP_CUDA(cudaGetSymbolAddress(&p, g_static_ws));
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return CSP_OK;
+}
+
+// Flags a lattice whose upper-face travel times are not zero (the solver reads f1 = 0 as
+// "no edge", and this entry point cannot zero them in a private copy).
+template <typename W>
+__global__ void k_check_upper_faces(const W *f1, long long V, int d, long long s0, long long s1, long long s2,
+                                    long long s3, long long n0, long long n1, long long n2, long long n3, Control *ctl)
+{
+    const long long st[4] = {s0, s1, s2, s3}, n[4] = {n0, n1, n2, n3};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d * V;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / V);
+        const long long v = i - k * V;
+        if ((v / st[k]) % n[k] == n[k] - 1 && f1[i] != 0) atomicExch(&ctl->status_in, ST_INVALID);
+    }
+}
+
+}  // namespace
+
+extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void *f1_dev, const void *f2_dev,
+                                       int weight_bytes, const int64_t *A_dev, int64_t nA, const int64_t *B_dev,
+                                       int64_t nB, int64_t M, int64_t max_cycles, void *stream, int64_t *result_dev)
+{
+    if (!extents || !f1_dev || !f2_dev || !A_dev || !B_dev || !result_dev || d < 1 || d > 4 ||
+        (weight_bytes != 1 && weight_bytes != 2) || nA < 1 || nB < 1 || M >= (1ll << 31) || M < -(1ll << 31) + 1)
+        return CSP_ERR_INVALID;
+    int64_t V = 1, ext[4] = {1, 1, 1, 1};
+    int stride[4] = {0, 0, 0, 0};
+    for (int k = 0; k < d; k++) {
+        if (extents[k] < 1 || extents[k] >= (1ll << 28)) return CSP_ERR_INVALID;
+        ext[k] = extents[k];
+        stride[k] = (int)V;
+        V *= extents[k];
+        if (V >= (1ll << 28)) return CSP_ERR_INVALID;
+    }
+    // carve the static array: per-vertex arrays, control block, then two pool buffers
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
+                 o_trig = take(V * 4), o_ctl = take(sizeof(Control));
+    const size_t kMinPool = 1024;
+    if (off + 2 * 3 * kMinPool * 4 + 3 * 2 * 256 > kStaticBytes) {
+        g_last_error = "csp_solve_static: lattice too large for the static workspace (" +
+                       std::to_string(kStaticBytes >> 20) + " MiB)";
+        return CSP_ERR_INVALID;
+    }
+    const size_t pool_cap = std::min<size_t>((kStaticBytes - off - 6 * 256) / 24, 0xF0000000ull);
+    size_t o_pool[2][3];
+    for (int b = 0; b < 2; b++)
+        for (int f = 0; f < 3; f++) o_pool[b][f] = take(pool_cap * 4);
+    if (off > kStaticBytes) {
+        g_last_error = "csp_solve_static: workspace layout exceeds the static array";
+        return CSP_ERR_INVALID;
+    }
+    void *base = nullptr;
+    csp_status st = static_workspace_address(&base);
+    if (st != CSP_OK) return st;
+    char *b = (char *)base;
+    int32_t *label = (int32_t *)(b + o_label);
+    unsigned long long *offer = (unsigned long long *)(b + o_offer);
+    uint32_t *isB = (uint32_t *)(b + o_isB);
+    int32_t *trig = (int32_t *)(b + o_trig);
+    Control *ctl = (Control *)(b + o_ctl);
+
+    cudaStream_t s = (cudaStream_t)stream;
+    CSP_CUDA(cudaMemsetAsync(label, 0, V * 4, s));
+    CSP_CUDA(cudaMemsetAsync(offer, 0, V * 8, s));
+    CSP_CUDA(cudaMemsetAsync(isB, 0, ((V + 31) / 32) * 4, s));
+    CSP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Control), s));
+    int dev = 0;
+    CSP_CUDA(cudaGetDevice(&dev));
+    const int sms = num_sms(dev);
+    k_reset<<<1, 32, 0, s>>>(ctl, nullptr, 0);  // counters; the tag is not used without a trace
+    k_tag_fix<<<1, 1, 0, s>>>(ctl);
+    const long long n[4] = {ext[0], ext[1], ext[2], ext[3]};
+    const long long stl[4] = {stride[0], stride[1], stride[2], stride[3]};
+    const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * 4, (d * V + 255) / 256));
+    if (weight_bytes == 1)
+        k_check_upper_faces<uint8_t><<<cblocks, 256, 0, s>>>((const uint8_t *)f1_dev, V, d, stl[0], stl[1], stl[2],
+                                                             stl[3], n[0], n[1], n[2], n[3], ctl);
+    else
+        k_check_upper_faces<uint16_t><<<cblocks, 256, 0, s>>>((const uint16_t *)f1_dev, V, d, stl[0], stl[1], stl[2],
+                                                              stl[3], n[0], n[1], n[2], n[3], ctl);
+    k_mark_B<<<(int)std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nB + 255) / 256)), 256, 0, s>>>(B_dev, nB, isB,
+                                                                                                     V, ctl);
+    k_mark_A<<<(int)std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nA + 255) / 256)), 256, 0, s>>>(
+        A_dev, nA, isB, V, (int)M, label, offer, trig, ctl);
+    CSP_CUDA(cudaGetLastError());
+
+    const void *fn = pick_kernel(d, weight_bytes, false);
+    int per_sm = 0;
+    CSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TPB, kSmem));
+    if (per_sm < 1) {
+        g_last_error = "persistent kernel does not fit on an SM";
+        return CSP_ERR_CUDA;
+    }
+    const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, V / 4096));
+    Params<uint8_t> P8{};
+    Params<uint16_t> P16{};
+    auto fill = [&](auto &P) {
+        using W = std::remove_cv_t<std::remove_pointer_t<decltype(P.f1)>>;
+        P.f1 = (const W *)f1_dev;
+        P.f2 = (const W *)f2_dev;
+        P.V = V;
+        for (int k = 0; k < 4; k++) P.stride[k] = stride[k];
+        P.label = label;
+        P.offer = offer;
+        P.isB = isB;
+        P.stamp = nullptr;
+        P.trig = trig;
+        P.trig_cap = (unsigned int)V;
+        for (int q = 0; q < 2; q++) {
+            P.ed[q] = (uint32_t *)(b + o_pool[q][0]);
+            P.qa[q] = (int32_t *)(b + o_pool[q][1]);
+            P.ta[q] = (int32_t *)(b + o_pool[q][2]);
+        }
+        P.pool_cap = (unsigned int)pool_cap;
+        P.ctl = ctl;
+        P.trace = nullptr;
+        P.trace_cap = 0;
+        P.result_dev = (long long *)result_dev;
+        P.M = (int)M;
+        P.max_cycles = max_cycles > 0 ? max_cycles : 0;
+        P.budget_ns = 120ull * 1000000000ull;
+    };
+    void *args[1];
+    if (weight_bytes == 1) {
+        fill(P8);
+        args[0] = &P8;
+    } else {
+        fill(P16);
+        args[0] = &P16;
+    }
+    CSP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(TPB), args, kSmem, s));
+    return CSP_OK;
+}

@@ -147,9 +147,9 @@ csp_status csp_solve_async(csp_lattice *lat, const int64_t *A_dev, int64_t nA, c
  *   M, max_cycles    as for csp_solve (max_cycles 0 = no limit).
  *   stream           cudaStream_t or NULL.
  *   result_dev       device record of 16 int64, laid out as for csp_solve_async.
- * Enqueues the solve and returns without waiting.  The layout needs 16.2 bytes per vertex
- * plus 24 bytes per flow-pool slot (two buffers); whatever the vertex arrays leave of the
- * static array becomes the flow pool.  A lattice whose vertex arrays do not fit is
+ * Enqueues the solve and returns without waiting.  The layout needs 28.125 + 8d bytes per
+ * vertex (labels, offers, B bitmap, arrival list, a 16-byte edge record; 16 more for
+ * 16-bit weights with d >= 3) plus 24 bytes per flow-pool slot (two buffers); whatever the vertex arrays leave of the static array becomes the flow pool.  A lattice whose vertex arrays do not fit is
  * rejected with CSP_ERR_INVALID (csp_last_error() says so); a solve whose flows do not fit
  * reports CSP_ERR_CAPACITY in result_dev[0].  No trace is recorded.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) for that device;

@@ -1,13 +1,15 @@
 // Device-side building blocks of the water-flow cycle (arXiv 1511.06441, Algorithm 1):
 // the flow-pool sweep (Steps 1-3 and 7-9), the launch phase (Steps 2, 4, 5 and the
-// label part of Step 8), block-level compaction and a spin-limited grid barrier.
+// label part of Step 8), block-level compaction, a TMA (bulk-copy) tile pipeline and a
+// spin-limited grid barrier.
 //
 // Data layout in HBM (one solve):
 //   label[V]  int32   committed labels, frozen while the pool is swept
 //   offer[V]  uint64  running max of (quality << 32 | ~(src*8 + dir)) over all arrivals;
 //                     its high half equals label[] at every cycle boundary
 //   isB[V/32] uint32  bitmap of B
-//   trig[]    int32   vertices whose label improves in the current cycle
+//   srcbits   uint32  bitmap of the sources of live flows (trace mode), cleared each pass
+//   cand[]    uint32  arrivals of the current cycle (flow word ed of each arriving flow)
 //   pool[2]   SoA     ed = dst << 3 | direction back to the source (uint32),
 //                     qa = quality on arrival (int32), ta = arrival time (int32)
 // A flow is the paper's water flow on an active (or phantom) edge: it left its source
@@ -19,55 +21,95 @@
 
 namespace csp {
 
-constexpr int TPB = 512;            // threads per CTA
-constexpr int IPT = 4;              // items per thread per tile
+#ifndef CSP_TPB
+#define CSP_TPB 512
+#endif
+#ifndef CSP_IPT
+#define CSP_IPT 4
+#endif
+#ifndef CSP_MIN_CTAS_PER_SM
+#define CSP_MIN_CTAS_PER_SM 2
+#endif
+constexpr int TPB = CSP_TPB;        // threads per CTA
+constexpr int IPT = CSP_IPT;        // items per thread per tile
 constexpr int TILE = TPB * IPT;     // items per tile
 constexpr int NWARP = TPB / 32;
 constexpr int TIME_LIMIT = 1 << 30; // arrival times must stay below this
+constexpr int POOL_PAD = 64;        // extra elements after each pool array (bulk copies round up)
 
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_OOM = 2, ST_CUDA = 3, ST_CAPACITY = 4, ST_TIMEOUT = 5, ST_BARRIER = 6 };
 
 // result record (int64): index of each field
 enum : int {
     R_STATUS = 0, R_F1, R_X, R_XSRC, R_XDIR, R_F2, R_CYCLES, R_UPDATES, R_LAUNCHED, R_PASSES,
-    R_MAXPOOL, R_TRACELEN, R_NEXTTAG, R_ARRIVALS, R_IMPROVED, R_COUNT = 16
+    R_MAXPOOL, R_TRACELEN, R_RESERVED, R_ARRIVALS, R_IMPROVED, R_COUNT = 16
 };
 
+__host__ __device__ __forceinline__ unsigned int lo32(unsigned long long x) { return (unsigned int)(x & 0xffffffffull); }
+__host__ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return (unsigned int)(x >> 32); }
+
+// Pass counters.  Every field that CTAs update concurrently sits on its own 128-byte line
+// (L2 atomics on one line serialise), and pairs updated together are packed into one
+// 64-bit word so that one atomic serves both.
 struct Counters {
-    unsigned long long n_live;    // live flows seen by the sweep
-    unsigned long long launched;  // flows emitted by the launch phase
-    unsigned long long xkey;      // max over improved B vertices of (label << 32 | ~id)
-    unsigned int n_out;           // flows written to the output pool
-    unsigned int n_trig;          // triggered vertices appended
-    unsigned int arrivals;        // live flows that arrived at the cycle time
-    unsigned int n_active;        // distinct sources of live flows (trace mode)
-    unsigned int overflow;        // an output list ran out of room
-    int min_ta;                   // smallest arrival time written to the output pool
-    unsigned int abort;           // set by the leader when the solve exceeded its time budget
-    unsigned int pad;
+    alignas(128) unsigned long long out_cand;  // low 32: flows written to the output pool; high 32: arrivals listed
+    alignas(128) unsigned long long live;      // live flows seen by the sweep
+    alignas(128) unsigned long long lau_imp;   // low 32: flows launched; high 32: vertices improved
+    alignas(128) unsigned long long xkey;      // max over improved B vertices of (label << 32 | ~id)
+    alignas(128) int min_ta;                   // smallest arrival time written to the output pool
+    alignas(128) unsigned int n_active;        // distinct sources of live flows (trace mode)
+    alignas(128) unsigned int overflow;        // an output list ran out of room
+    unsigned int abort;                        // set by the leader when the solve exceeded its time budget
+};
+
+constexpr int NRELEASE = 32;  // copies of the barrier's release word, one per 128-byte line
+
+struct ReleaseWord {
+    alignas(128) unsigned long long epoch;
 };
 
 struct Control {
-    unsigned long long bar;       // grid-barrier arrivals, monotonic within a solve
-    int err;                      // set when a barrier wait gives up
-    int status_in;                // set by the set-up kernels (invalid ids, A and B overlap)
-    unsigned int tag;             // next unused stamp tag (kept across solves)
-    unsigned int pad;
+    alignas(128) unsigned long long bar;  // grid-barrier arrivals, monotonic within a solve
+    alignas(128) int err;                 // set when a barrier or copy wait gives up
+    int status_in;                        // set by the set-up kernels (invalid ids, A and B overlap)
+    ReleaseWord release[NRELEASE];        // last barrier epoch released (one copy per line)
     Counters cnt[2];
-    long long out[R_COUNT];
+    alignas(128) long long out[R_COUNT];
+};
+
+// Per-vertex edge record: (f1, f2) of the 2d edges of a vertex in direction order,
+// f1 = 0 for a missing edge (absent, or leaving the box).  8-bit weights: 2 bytes per
+// direction, one 16-byte record for d <= 4.  16-bit weights: 4 bytes per direction,
+// 16 bytes for d <= 2 and 32 bytes for d <= 4.
+template <typename W, int D>
+struct EdgeRecord {
+    static constexpr int BYTES = (int)sizeof(W) * 2 * 2 * D <= 16 ? 16 : 32;
+    static constexpr int VEC = BYTES / 16;  // uint4 loads per record
+    uint4 raw[VEC];
+    __device__ __forceinline__ int f1(int dir) const
+    {
+        const W *w = reinterpret_cast<const W *>(raw);
+        return (int)w[2 * dir];
+    }
+    __device__ __forceinline__ int f2(int dir) const
+    {
+        const W *w = reinterpret_cast<const W *>(raw);
+        return (int)w[2 * dir + 1];
+    }
 };
 
 template <typename W>
 struct Params {
     const W *f1, *f2;              // [d][V] travel time, weight of edge (v, v + e_k)
+    const uint4 *rec;              // per-vertex edge records (EdgeRecord<W, d>)
     long long V;
     int stride[4];
     int32_t *label;
     unsigned long long *offer;
     const uint32_t *isB;
-    uint32_t *stamp;               // distinct-source stamps (trace mode)
-    int32_t *trig;
-    unsigned int trig_cap;
+    uint32_t *srcbits;             // trace mode: sources of live flows, (V + 31) / 32 words
+    uint32_t *cand;                // arrivals of the current cycle (the sources of A at the seed)
+    unsigned int cand_cap;
     uint32_t *ed[2];
     int32_t *qa[2];
     int32_t *ta[2];
@@ -79,6 +121,18 @@ struct Params {
     int M;
     long long max_cycles;
     unsigned long long budget_ns;  // wall-clock budget of one launch (watchdog)
+};
+
+// Dynamic shared memory of the cycle kernel: two input stages filled by bulk copies,
+// one output staging tile, and the two stage barriers.
+struct Smem {
+    uint32_t in_ed[2][TILE];
+    int32_t in_qa[2][TILE];
+    int32_t in_ta[2][TILE];
+    uint32_t out_ed[TILE];
+    int32_t out_qa[TILE];
+    int32_t out_ta[TILE];
+    unsigned long long mbar[2];
 };
 
 // ---------------------------------------------------------------- small helpers
@@ -97,6 +151,16 @@ __device__ __forceinline__ int dir_offset(const int (&stride)[4], unsigned r)
 __device__ __forceinline__ bool in_set(const uint32_t *bits, uint32_t v)
 {
     return (__ldg(bits + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// x code of a flow arriving at dst from direction r (r = direction from dst back to the
+// source): ~(src * 8 + dir), dir = r ^ 1 the direction from the source to dst.
+template <int D>
+__device__ __forceinline__ uint32_t arrival_code(const int (&stride)[4], uint32_t ed)
+{
+    const uint32_t dst = ed >> 3, r = ed & 7u;
+    const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(stride, r));
+    return 0xffffffffu - (src * 8u + (r ^ 1u));
 }
 
 // Exclusive block-wide prefix sum of x; *total receives the block sum.
@@ -132,8 +196,12 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Grid-wide barrier for a cooperative (co-resident) launch.  The wait gives up after
-// ~4 s or 2^26 polls, sets ctl->err and returns false; every CTA then leaves the kernel.
+// Grid-wide barrier for a cooperative (co-resident) launch.  Arrivals are counted on one
+// word; the last CTA to arrive publishes the new epoch to NRELEASE release words on
+// separate lines, and every CTA polls its own copy (with a short sleep between polls).
+// Spreading the polls keeps the waiting CTAs from saturating one L2 slice while the
+// slowest CTAs are still working.  The wait gives up after ~4 s or 2^26 polls, sets
+// ctl->err and returns false; every CTA then leaves the kernel.
 __device__ __forceinline__ bool grid_sync(Control *ctl, unsigned long long &epoch)
 {
     __shared__ int s_ok;
@@ -142,20 +210,32 @@ __device__ __forceinline__ bool grid_sync(Control *ctl, unsigned long long &epoc
         epoch += 1;
         const unsigned long long target = epoch * gridDim.x;
         __threadfence();
-        atomicAdd(&ctl->bar, 1ull);
+        const unsigned long long arrived = atomicAdd(&ctl->bar, 1ull) + 1ull;
         int ok = 1;
-        const unsigned long long t0 = globaltimer_ns();
-        for (unsigned int spin = 0;; ++spin) {
-            unsigned long long seen;
-            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(&ctl->bar) : "memory");
-            if (seen >= target) break;
-            if (*(volatile int *)&ctl->err) { ok = 0; break; }
-            if (spin > (1u << 26) || (spin & 1023u) == 0 && globaltimer_ns() - t0 > 4000000000ull) {
-                atomicExch(&ctl->err, 1);
-                ok = 0;
-                break;
+        if (arrived == target) {
+            // the last arrival has seen every other CTA's (fenced) arrival: one release
+            // fence, then plain strong stores of the epoch (the pollers load with acquire)
+            __threadfence();
+            for (int i = 0; i < NRELEASE; i++)
+                asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&ctl->release[i].epoch), "l"(epoch)
+                             : "memory");
+        } else {
+            const unsigned long long *word = &ctl->release[blockIdx.x % NRELEASE].epoch;
+            const unsigned long long t0 = globaltimer_ns();
+            for (unsigned int spin = 0;; ++spin) {
+                unsigned long long seen;
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(word) : "memory");
+                if (seen >= epoch) break;
+                if ((spin & 63u) == 63u) {
+                    if (*(volatile int *)&ctl->err) { ok = 0; break; }
+                    if (spin > (1u << 26) || globaltimer_ns() - t0 > 4000000000ull) {
+                        atomicExch(&ctl->err, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(64);
             }
-            if (spin > 64) __nanosleep(64);
         }
         __threadfence();
         s_ok = ok;
@@ -164,77 +244,173 @@ __device__ __forceinline__ bool grid_sync(Control *ctl, unsigned long long &epoc
     return s_ok != 0;
 }
 
+// ---------------------------------------------------------------- bulk copies (TMA)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 1-D bulk copy global -> shared, completion counted on mbar (bytes: multiple of 16,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Thread 0: starts the bulk copy of pool tile `tile` (buffer ib) into input stage s.
+template <typename W>
+__device__ __forceinline__ void issue_tile(const Params<W> &P, Smem &sm, int s, int ib, uint32_t tile, uint32_t n_in)
+{
+    const uint32_t start = tile * (uint32_t)TILE;
+    const uint32_t n = min((uint32_t)TILE, n_in - start);
+    const uint32_t bytes = ((n + 3u) & ~3u) * 4u;  // round up to 16 bytes (pool arrays are padded)
+    mbar_expect_tx(&sm.mbar[s], 3u * bytes);
+    bulk_g2s(sm.in_ed[s], P.ed[ib] + start, bytes, &sm.mbar[s]);
+    bulk_g2s(sm.in_qa[s], P.qa[ib] + start, bytes, &sm.mbar[s]);
+    bulk_g2s(sm.in_ta[s], P.ta[ib] + start, bytes, &sm.mbar[s]);
+}
+
+// All threads wait for stage s (bounded).  Returns false, uniformly across the CTA, if
+// the copy did not complete in time (ctl->err is then set).
+__device__ __forceinline__ bool wait_stage(Smem &sm, int s, uint32_t parity, Control *ctl)
+{
+    bool ok = false;
+    for (uint32_t i = 0; i < (1u << 22); i++)
+        if (mbar_try_wait(&sm.mbar[s], parity)) {
+            ok = true;
+            break;
+        }
+    const int bad = __syncthreads_or(!ok);
+    if (bad) {
+        if (threadIdx.x == 0) atomicExch(&ctl->err, 1);
+        // give a late copy a last chance to land before the CTA leaves
+        for (uint32_t i = 0; i < (1u << 20) && !mbar_try_wait(&sm.mbar[s], parity); i++) {
+        }
+        return false;
+    }
+    return true;
+}
+
 struct LocalStats {
-    uint32_t live, arrivals, active, launched;
+    uint32_t live, launched, improved, active;
     int min_ta;
 };
 
-// Adds this block's statistics to the pass counters (one global atomic per field per CTA).
+// Adds this block's statistics to the pass counters (one global atomic per word per CTA).
 __device__ __forceinline__ void flush_stats(const LocalStats &st, Counters *C)
 {
-    __shared__ unsigned long long s_live, s_launched;
-    __shared__ unsigned int s_arr, s_act;
+    __shared__ unsigned long long s_live, s_li;
+    __shared__ unsigned int s_act;
     __shared__ int s_min;
     if (threadIdx.x == 0) {
         s_live = 0;
-        s_launched = 0;
-        s_arr = 0;
+        s_li = 0;
         s_act = 0;
         s_min = INT_MAX;
     }
     __syncthreads();
-    uint32_t live = st.live, arr = st.arrivals, act = st.active, lau = st.launched;
+    uint32_t live = st.live, lau = st.launched, imp = st.improved, act = st.active;
     int mn = st.min_ta;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         live += __shfl_xor_sync(0xffffffffu, live, o);
-        arr += __shfl_xor_sync(0xffffffffu, arr, o);
-        act += __shfl_xor_sync(0xffffffffu, act, o);
         lau += __shfl_xor_sync(0xffffffffu, lau, o);
+        imp += __shfl_xor_sync(0xffffffffu, imp, o);
+        act += __shfl_xor_sync(0xffffffffu, act, o);
         mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (live) atomicAdd(&s_live, (unsigned long long)live);
-        if (lau) atomicAdd(&s_launched, (unsigned long long)lau);
-        if (arr) atomicAdd(&s_arr, arr);
+        if (lau | imp) atomicAdd(&s_li, (unsigned long long)lau | ((unsigned long long)imp << 32));
         if (act) atomicAdd(&s_act, act);
         if (mn != INT_MAX) atomicMin(&s_min, mn);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (s_live) atomicAdd(&C->n_live, s_live);
-        if (s_launched) atomicAdd(&C->launched, s_launched);
-        if (s_arr) atomicAdd(&C->arrivals, s_arr);
+        if (s_live) atomicAdd(&C->live, s_live);
+        if (s_li) atomicAdd(&C->lau_imp, s_li);
         if (s_act) atomicAdd(&C->n_active, s_act);
         if (s_min != INT_MAX) atomicMin(&C->min_ta, s_min);
     }
 }
 
-// Staging area for one tile of output flows (coalesced write-out).
-struct TileStage {
-    uint32_t ed[TILE];
-    int32_t qa[TILE];
-    int32_t ta[TILE];
-};
-
-// Appends the flows marked keep[i] (per thread, IPT slots) to the output pool.
-// Block-compacted: one atomicAdd per tile reserves room; flows are staged in shared
-// memory and written out contiguously.
-template <typename W>
-__device__ __forceinline__ void append_flows(const Params<W> &P, int ob, Counters *C, const bool (&keep)[IPT],
-                                             const uint32_t (&e)[IPT], const int32_t (&q)[IPT],
-                                             const int32_t (&t)[IPT], uint32_t nk, TileStage &stage,
-                                             uint32_t *s_warp, uint32_t *s_base)
+// Reserves room for this tile's output with ONE 64-bit atomic on (flows | arrivals << 32):
+// a block-wide scan of the packed per-thread counts gives each thread its offsets.
+// s_base[0..1] receive the tile's global bases (valid after the next __syncthreads).
+__device__ __forceinline__ void reserve_tile(uint32_t nk, uint32_t nt, Counters *C, uint32_t &pk, uint32_t &pt,
+                                             uint32_t &tk, uint32_t &tt, uint32_t *s_warp, uint32_t *s_base)
 {
     uint32_t total;
-    uint32_t pos = block_scan_excl(nk, total, s_warp);
-    if (threadIdx.x == 0) s_base[0] = total ? atomicAdd(&C->n_out, total) : 0u;
+    const uint32_t pre = block_scan_excl(nk | (nt << 16), total, s_warp);
+    pk = pre & 0xffffu;
+    pt = pre >> 16;
+    tk = total & 0xffffu;
+    tt = total >> 16;
+    if (threadIdx.x == 0) {
+        unsigned long long old = 0;
+        if (tk | tt) old = atomicAdd(&C->out_cand, (unsigned long long)tk | ((unsigned long long)tt << 32));
+        s_base[0] = lo32(old);
+        s_base[1] = hi32(old);
+    }
+}
+
+// Writes the flows marked keep[i] (per thread, IPT slots) to the output pool: staged in
+// shared memory at the scanned offsets, then written out contiguously.
+template <typename W>
+__device__ __forceinline__ void write_flows(const Params<W> &P, int ob, Counters *C, const bool (&keep)[IPT],
+                                            const uint32_t (&e)[IPT], const int32_t (&q)[IPT],
+                                            const int32_t (&t)[IPT], uint32_t pos, uint32_t total, Smem &sm,
+                                            const uint32_t *s_base)
+{
 #pragma unroll
     for (int i = 0; i < IPT; i++)
         if (keep[i]) {
-            stage.ed[pos] = e[i];
-            stage.qa[pos] = q[i];
-            stage.ta[pos] = t[i];
+            sm.out_ed[pos] = e[i];
+            sm.out_qa[pos] = q[i];
+            sm.out_ta[pos] = t[i];
             pos++;
         }
     __syncthreads();
@@ -246,9 +422,9 @@ __device__ __forceinline__ void append_flows(const Params<W> &P, int ob, Counter
             uint32_t *oe = P.ed[ob];
             int32_t *oq = P.qa[ob], *ot = P.ta[ob];
             for (uint32_t j = threadIdx.x; j < total; j += TPB) {
-                oe[base + j] = stage.ed[j];
-                oq[base + j] = stage.qa[j];
-                ot[base + j] = stage.ta[j];
+                oe[base + j] = sm.out_ed[j];
+                oq[base + j] = sm.out_qa[j];
+                ot[base + j] = sm.out_ta[j];
             }
         }
     }
@@ -258,146 +434,241 @@ __device__ __forceinline__ void append_flows(const Params<W> &P, int ob, Counter
 // ---------------------------------------------------------------- the sweep
 
 // One pass over the flow pool (Steps 1-3 and 7-9 of the paper).  For every flow:
-//   dead   if qa <= label[dst] (labels of the end of the previous cycle): dropped;
+//   dead    if qa <= label[dst] (labels of the end of the previous cycle): dropped;
 //   arrives if it is live and ta == Tg: offers (qa, ~(src*8+dir)) to dst with a 64-bit
-//          atomicMax; the first arrival at dst this cycle (the one that sees the old
-//          offer still equal to the label) appends dst to the triggered list;
+//           atomic max (no return value needed) and is listed as a candidate; the launch
+//           phase finds, for each improved vertex, the one candidate that won;
 //   survives otherwise: copied to the output pool.
-// With TRACE, live flows also stamp their source to count distinct active vertices.
+// Pool tiles arrive by bulk copies into two shared-memory stages: while a tile is
+// processed the next one is already in flight.  With TRACE, live flows set their source's
+// bit in srcbits (counted by the launch phase).
+// Returns false if a copy wait timed out (ctl->err set).
 template <int D, typename W, bool TRACE>
-__device__ void sweep(const Params<W> &P, int ib, uint32_t n_in, int Tg, Counters *C, uint32_t tag,
-                      LocalStats &st, TileStage &stage, uint32_t *s_warp, uint32_t *s_base)
+__device__ bool sweep(const Params<W> &P, int ib, uint32_t n_in, int Tg, Counters *C, LocalStats &st, Smem &sm,
+                      uint32_t (&parity)[2], uint32_t *s_warp, uint32_t *s_base)
 {
-    const uint32_t *__restrict__ ie = P.ed[ib];
-    const int32_t *__restrict__ iq = P.qa[ib];
-    const int32_t *__restrict__ it = P.ta[ib];
     const int ob = ib ^ 1;
-    for (uint32_t base = blockIdx.x * TILE; base < n_in; base += gridDim.x * TILE) {
+    const uint32_t G = gridDim.x;
+    const uint32_t n_tiles = (n_in + TILE - 1) / TILE;
+    if (threadIdx.x == 0 && blockIdx.x < n_tiles) {
+        fence_proxy_async_global();  // pool written by ordinary stores in the previous pass
+        issue_tile(P, sm, 0, ib, blockIdx.x, n_in);
+        if (blockIdx.x + G < n_tiles) issue_tile(P, sm, 1, ib, blockIdx.x + G, n_in);
+    }
+    uint32_t k = 0;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += G, k++) {
+        const int s = (int)(k & 1u);
+        if (!wait_stage(sm, s, parity[s], P.ctl)) return false;
+        parity[s] ^= 1u;
+        const uint32_t base = tile * (uint32_t)TILE;
         uint32_t e[IPT];
         int32_t q[IPT], t[IPT], L[IPT];
-        bool keep[IPT], trig[IPT];
+        bool keep[IPT], arr[IPT];
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
-            const uint32_t idx = base + i * TPB + threadIdx.x;
-            keep[i] = trig[i] = false;
-            e[i] = 0;
-            q[i] = 0;
-            t[i] = 0;
-            if (idx < n_in) {
-                e[i] = __ldcg(ie + idx);
-                q[i] = __ldcg(iq + idx);
-                t[i] = __ldcg(it + idx);
-            }
+            const uint32_t j = i * TPB + threadIdx.x;
+            const bool in = base + j < n_in;
+            e[i] = in ? sm.in_ed[s][j] : 0u;
+            q[i] = in ? sm.in_qa[s][j] : 0;
+            t[i] = in ? sm.in_ta[s][j] : 0;
+        }
+        __syncthreads();  // stage s fully read: refill it with tile + 2G
+        if (threadIdx.x == 0 && tile + 2 * G < n_tiles) {
+            fence_proxy_async_smem();
+            issue_tile(P, sm, s, ib, tile + 2 * G, n_in);
         }
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
-            const uint32_t idx = base + i * TPB + threadIdx.x;
             L[i] = INT_MAX;
-            if (idx < n_in) L[i] = __ldcg(P.label + (e[i] >> 3));
+            if (base + i * TPB + threadIdx.x < n_in) L[i] = __ldcg(P.label + (e[i] >> 3));
         }
         uint32_t nk = 0, nt = 0;
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
+            keep[i] = arr[i] = false;
             if (q[i] <= L[i]) continue;  // dead (or padding): removed
             st.live++;
-            const uint32_t dst = e[i] >> 3, r = e[i] & 7u;
-            const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(P.stride, r));
+            const uint32_t dst = e[i] >> 3;
             if (TRACE) {
-                if (atomicExch(P.stamp + src, tag) != tag) st.active++;
+                const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(P.stride, e[i] & 7u));
+                atomicOr(P.srcbits + (src >> 5), 1u << (src & 31));
             }
             if (t[i] == Tg) {
-                st.arrivals++;
                 const unsigned long long key =
-                    ((unsigned long long)(uint32_t)q[i] << 32) | (0xffffffffu - (src * 8u + (r ^ 1u)));
-                const unsigned long long old = atomicMax(P.offer + dst, key);
-                if ((uint32_t)(old >> 32) == (uint32_t)L[i]) {
-                    trig[i] = true;
-                    nt++;
-                }
+                    ((unsigned long long)(uint32_t)q[i] << 32) | arrival_code<D>(P.stride, e[i]);
+                atomicMax(P.offer + dst, key);
+                arr[i] = true;
+                nt++;
             } else {
                 keep[i] = true;
                 nk++;
                 st.min_ta = min(st.min_ta, t[i]);
             }
         }
-        // triggered vertices: reserve with one atomic per tile, write directly
-        uint32_t ttot;
-        uint32_t tpos = block_scan_excl(nt, ttot, s_warp);
-        if (threadIdx.x == 0) s_base[1] = ttot ? atomicAdd(&C->n_trig, ttot) : 0u;
-        __syncthreads();
+        uint32_t pk, pt, tk, tt;
+        reserve_tile(nk, nt, C, pk, pt, tk, tt, s_warp, s_base);
+        __syncthreads();  // s_base (written by thread 0) is visible after this barrier
         if (nt) {
-            const uint32_t tb = s_base[1] + tpos;
+            const uint32_t cb = s_base[1] + pt;
 #pragma unroll
             for (int i = 0, j = 0; i < IPT; i++)
-                if (trig[i]) {
-                    if (tb + j < P.trig_cap) P.trig[tb + j] = (int32_t)(e[i] >> 3);
+                if (arr[i]) {
+                    if (cb + j < P.cand_cap) P.cand[cb + j] = e[i];
                     else atomicExch(&C->overflow, 1u);
                     j++;
                 }
         }
-        append_flows(P, ob, C, keep, e, q, t, nk, stage, s_warp, s_base);
+        write_flows(P, ob, C, keep, e, q, t, pk, tk, sm, s_base);
     }
+    return true;
 }
 
 // ---------------------------------------------------------------- the launch phase
 
-// For every triggered vertex v (items = (v, direction) pairs): commit its new label
-// (Step 8), record it if it is in B (Algorithm 2), and start a flow on every edge
-// (v, w) with Label(v) - f2 > Label(w) under the labels at the end of this cycle
-// (Steps 4-5; a flow on an edge that already carries water is the paper's phantom).
-template <int D, typename W>
-__device__ void launch(const Params<W> &P, int ob, uint32_t n_trig, int Time, Counters *C, LocalStats &st,
-                       TileStage &stage, uint32_t *s_warp, uint32_t *s_base)
+template <typename W, int D>
+__device__ __forceinline__ EdgeRecord<W, D> load_record(const uint4 *rec, uint32_t v)
 {
-    constexpr uint32_t ND = 2 * D;
-    const uint32_t n_items = n_trig * ND;
-    for (uint32_t base = blockIdx.x * TILE; base < n_items; base += gridDim.x * TILE) {
-        uint32_t e[IPT];
-        int32_t q[IPT], t[IPT];
-        bool keep[IPT];
-        uint32_t nk = 0;
+    EdgeRecord<W, D> r;
 #pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint32_t j = base + i * TPB + threadIdx.x;
-            keep[i] = false;
-            e[i] = 0;
-            q[i] = 0;
-            t[i] = 0;
-            if (j >= n_items) continue;
-            const uint32_t v = (uint32_t)__ldcg(P.trig + j / ND);
-            const uint32_t dir = j % ND;
-            const int Lv = (int)(__ldcg(P.offer + v) >> 32);
-            if (dir == 0) {
-                P.label[v] = Lv;
-                if (in_set(P.isB, v))
-                    atomicMax(&C->xkey, ((unsigned long long)(uint32_t)Lv << 32) | (0xffffffffu - v));
-            }
-            const uint32_t k = dir >> 1;
-            const int s = dir_offset<D>(P.stride, dir);
-            uint32_t w, slot;
-            if (dir & 1) {
-                if (v < (uint32_t)(-s)) continue;  // lower face of the box: no edge
-                w = v + s;
-                slot = k * (uint32_t)P.V + w;
-            } else {
-                w = v + s;
-                slot = k * (uint32_t)P.V + v;       // upper-face entries are zero: no edge
-            }
-            const int t1 = (int)__ldg(P.f1 + slot);
-            if (t1 == 0) continue;
-            const int qa = Lv - (int)__ldg(P.f2 + slot);
-            const int Lw = (int)(__ldcg(P.offer + w) >> 32);
-            if (qa > Lw) {
-                keep[i] = true;
-                nk++;
-                e[i] = (w << 3) | (dir ^ 1u);
-                q[i] = qa;
-                t[i] = Time + t1;
-                st.min_ta = min(st.min_ta, t[i]);
-                st.launched++;
+    for (int i = 0; i < EdgeRecord<W, D>::VEC; i++) r.raw[i] = __ldg(rec + (size_t)v * EdgeRecord<W, D>::VEC + i);
+    return r;
+}
+
+// Label of every neighbour of v (clamped index where the edge leaves the box; the value
+// is then ignored because the record's f1 is 0).
+template <int D>
+__device__ __forceinline__ void neighbour_labels(const unsigned long long *offer, const int (&stride)[4], uint32_t V,
+                                                 uint32_t v, int (&Lw)[2 * D])
+{
+#pragma unroll
+    for (int dir = 0; dir < 2 * D; dir++) {
+        const uint32_t w = v + dir_offset<D>(stride, dir);
+        Lw[dir] = __ldcg(reinterpret_cast<const int *>(offer + (w < V ? w : v)) + 1);  // label half of offer[w]
+    }
+}
+
+// Water of quality Lv leaves v along each edge (v, w) with Lv - f2 > Label(w): returns
+// the bit mask of those directions (Steps 4-5).
+template <typename W, int D>
+__device__ __forceinline__ uint32_t launch_mask(const EdgeRecord<W, D> &r, int Lv, const int (&Lw)[2 * D])
+{
+    uint32_t mask = 0;
+#pragma unroll
+    for (int dir = 0; dir < 2 * D; dir++)
+        if (r.f1(dir) != 0 && Lv - r.f2(dir) > Lw[dir]) mask |= 1u << dir;
+    return mask;
+}
+
+// Appends the flows of mask (per thread, one source vertex v) to the output pool through
+// a block-compacted staging area (the sweep's input stages, free during this phase).
+template <typename W, int D>
+__device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters *C, uint32_t v, int Lv,
+                                           const EdgeRecord<W, D> &r, uint32_t mask, int Time, LocalStats &st,
+                                           Smem &sm, uint32_t *s_warp, uint32_t *s_base)
+{
+    static_assert(TPB * 2 * D <= 2 * TILE, "launch staging needs TPB * 2d <= 2 * TILE");
+    uint32_t *stage_ed = &sm.in_ed[0][0];
+    int32_t *stage_qa = &sm.in_qa[0][0], *stage_ta = &sm.in_ta[0][0];
+    const uint32_t nk = __popc(mask);
+    uint32_t pos, pt, total, tt;
+    reserve_tile(nk, 0, C, pos, pt, total, tt, s_warp, s_base);
+#pragma unroll
+    for (int dir = 0; dir < 2 * D; dir++)
+        if (mask & (1u << dir)) {
+            const uint32_t w = v + dir_offset<D>(P.stride, dir);
+            const int t = Time + r.f1(dir);
+            stage_ed[pos] = (w << 3) | (uint32_t)(dir ^ 1);
+            stage_qa[pos] = Lv - r.f2(dir);
+            stage_ta[pos] = t;
+            pos++;
+            st.min_ta = min(st.min_ta, t);
+            st.launched++;
+        }
+    __syncthreads();
+    const uint32_t base = s_base[0];
+    if (total) {
+        if ((unsigned long long)base + total > P.pool_cap) {
+            if (threadIdx.x == 0) atomicExch(&C->overflow, 1u);
+        } else {
+            uint32_t *oe = P.ed[ob];
+            int32_t *oq = P.qa[ob], *ot = P.ta[ob];
+            for (uint32_t j = threadIdx.x; j < total; j += TPB) {
+                oe[base + j] = stage_ed[j];
+                oq[base + j] = stage_qa[j];
+                ot[base + j] = stage_ta[j];
             }
         }
-        append_flows(P, ob, C, keep, e, q, t, nk, stage, s_warp, s_base);
+    }
+    __syncthreads();
+}
+
+// One thread per arrival candidate.  The candidate whose code equals the final offer word
+// of its destination v is the winner: v improved this cycle (Step 2).  The winner commits
+// the label (Step 8), records v if it is in B (Algorithm 2), and starts a flow on every
+// edge (v, w) with Label(v) - f2 > Label(w) under the labels at the end of this cycle
+// (Steps 4-5; a flow on an edge that already carries water is the paper's phantom).
+// Its loads (offer[v], the edge record, the 2d neighbour labels) are issued together.
+// With TRACE, also counts (and clears) the source bitmap filled by the sweep.
+template <int D, typename W, bool TRACE>
+__device__ void launch(const Params<W> &P, int ob, uint32_t n_cand, int Time, Counters *C, LocalStats &st, Smem &sm,
+                       uint32_t *s_warp, uint32_t *s_base)
+{
+    const uint32_t V = (uint32_t)P.V;
+    if (TRACE) {
+        const uint32_t words = (V + 31) / 32;
+        for (uint32_t w = blockIdx.x * TPB + threadIdx.x; w < words; w += gridDim.x * TPB) {
+            const uint32_t b = __ldcg(P.srcbits + w);
+            if (b) {
+                st.active += __popc(b);
+                P.srcbits[w] = 0u;
+            }
+        }
+    }
+    for (uint32_t base = blockIdx.x * TPB; base < n_cand; base += gridDim.x * TPB) {
+        const uint32_t j = base + threadIdx.x;
+        uint32_t v = 0, mask = 0;
+        int Lv = 0;
+        EdgeRecord<W, D> r{};
+        if (j < n_cand) {
+            const uint32_t ec = __ldcg(P.cand + j);
+            v = ec >> 3;
+            const uint32_t code = arrival_code<D>(P.stride, ec);
+            const unsigned long long ov = __ldcg(P.offer + v);
+            r = load_record<W, D>(P.rec, v);
+            int Lw[2 * D];
+            neighbour_labels<D>(P.offer, P.stride, V, v, Lw);
+            if (lo32(ov) == code) {  // the winning arrival at v
+                Lv = (int)hi32(ov);
+                P.label[v] = Lv;
+                st.improved++;
+                if (in_set(P.isB, v))
+                    atomicMax(&C->xkey, ((unsigned long long)(uint32_t)Lv << 32) | (0xffffffffu - v));
+                mask = launch_mask<W, D>(r, Lv, Lw);
+            }
+        }
+        emit_flows<W, D>(P, ob, C, v, Lv, r, mask, Time, st, sm, s_warp, s_base);
+    }
+}
+
+// Seed launch (Algorithm 3): water of quality M leaves every source a in A (listed in
+// cand as plain vertex ids, label M already set) along each edge with M - f2 > Label(w).
+template <int D, typename W>
+__device__ void seed(const Params<W> &P, uint32_t n_src, Counters *C, LocalStats &st, Smem &sm, uint32_t *s_warp,
+                     uint32_t *s_base)
+{
+    const uint32_t V = (uint32_t)P.V;
+    for (uint32_t base = blockIdx.x * TPB; base < n_src; base += gridDim.x * TPB) {
+        const uint32_t j = base + threadIdx.x;
+        uint32_t v = 0, mask = 0;
+        EdgeRecord<W, D> r{};
+        if (j < n_src) {
+            v = __ldcg(P.cand + j);
+            r = load_record<W, D>(P.rec, v);
+            int Lw[2 * D];
+            neighbour_labels<D>(P.offer, P.stride, V, v, Lw);
+            mask = launch_mask<W, D>(r, P.M, Lw);
+        }
+        emit_flows<W, D>(P, 0, C, v, P.M, r, mask, 0, st, sm, s_warp, s_base);
     }
 }
 

@@ -57,6 +57,8 @@ struct csp_lattice {
     int64_t V = 0;
     int device = 0;
     void *f1 = nullptr, *f2 = nullptr;  // device [d][V]
+    void *rec = nullptr;                // device per-vertex edge records
+    int rec_bytes = 16;
     unsigned long long flow_bound = 0;  // sum of f1 over directed edges: max flows alive
     // workspace
     void *ws = nullptr;
@@ -64,8 +66,9 @@ struct csp_lattice {
     int64_t pool_cap = 0;
     int32_t *label = nullptr;
     unsigned long long *offer = nullptr;
-    uint32_t *isB = nullptr, *stamp = nullptr;
-    int32_t *trig = nullptr;
+    uint32_t *isB = nullptr, *srcbits = nullptr;
+    uint32_t *cand = nullptr;
+    int64_t cand_cap = 0;
     uint32_t *ed[2] = {nullptr, nullptr};
     int32_t *qa[2] = {nullptr, nullptr}, *ta[2] = {nullptr, nullptr};
     Control *ctl = nullptr;
@@ -93,6 +96,33 @@ __global__ void k_zero_upper_faces(W *f1, W *f2, long long V, int d, long long s
     }
 }
 
+// Packs, for every vertex, the (f1, f2) of its 2d edges in direction order into one
+// record (f1 = 0 where the edge is absent or leaves the box).  Built once per upload.
+template <typename W>
+__global__ void k_build_records(const W *f1, const W *f2, long long V, int d, long long s0, long long s1, long long s2,
+                                long long s3, long long n0, long long n1, long long n2, long long n3, unsigned char *rec,
+                                int rec_bytes)
+{
+    const long long st[4] = {s0, s1, s2, s3}, n[4] = {n0, n1, n2, n3};
+    const int per = rec_bytes / (int)sizeof(W);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        W *out = reinterpret_cast<W *>(rec + v * rec_bytes);
+        for (int i = 0; i < per; i++) out[i] = 0;
+        for (int dir = 0; dir < 2 * d; dir++) {
+            const int k = dir >> 1;
+            const long long ck = (v / st[k]) % n[k];
+            long long slot = -1;
+            if (!(dir & 1) && ck + 1 < n[k]) slot = k * V + v;
+            if ((dir & 1) && ck > 0) slot = k * V + v - st[k];
+            if (slot < 0 || f1[slot] == 0) continue;
+            out[2 * dir] = f1[slot];
+            out[2 * dir + 1] = f2[slot];
+        }
+    }
+}
+
+int record_bytes(int d, int wbytes) { return wbytes * 4 * d <= 16 ? 16 : 32; }
+
 template <typename W>
 __global__ void k_flow_bound(const W *f1, long long n, unsigned long long *out)
 {
@@ -103,31 +133,22 @@ __global__ void k_flow_bound(const W *f1, long long n, unsigned long long *out)
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, 2ull * s);
 }
 
-// Resets the control block for a new solve; clears the stamp array when the tag
-// counter is about to wrap.
-__global__ void k_reset(Control *ctl, uint32_t *stamp, long long V)
+// Resets the control block for a new solve.
+__global__ void k_reset(Control *ctl)
 {
-    const bool wrap = ctl->tag > 0xF0000000u || ctl->tag == 0u;
-    if (wrap)
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
-            stamp[i] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->bar = 0;
         ctl->err = 0;
         ctl->status_in = 0;
+        for (int i = 0; i < NRELEASE; i++) ctl->release[i].epoch = 0;
         for (int b = 0; b < 2; b++) {
             Counters &c = ctl->cnt[b];
-            c.n_live = c.launched = c.xkey = 0;
-            c.n_out = c.n_trig = c.arrivals = c.n_active = c.overflow = c.abort = 0;
+            c.out_cand = c.live = c.lau_imp = c.xkey = 0;
+            c.n_active = c.overflow = c.abort = 0;
             c.min_ta = INT_MAX;
         }
         for (int i = 0; i < R_COUNT; i++) ctl->out[i] = 0;
     }
-}
-
-__global__ void k_tag_fix(Control *ctl)
-{
-    if (ctl->tag > 0xF0000000u || ctl->tag == 0u) ctl->tag = 1;
 }
 
 // Marks B in the bitmap; out-of-range ids make the solve invalid.
@@ -141,9 +162,9 @@ __global__ void k_mark_B(const int64_t *B, long long nB, uint32_t *isB, long lon
 }
 
 // Initialization (Algorithm 3): Label(a) = M for a in A (the offer word mirrors it);
-// each distinct source is listed once as the "triggered" set of the seed launch.
+// each distinct source is listed once (in the candidate list) for the seed launch.
 __global__ void k_mark_A(const int64_t *A, long long nA, const uint32_t *isB, long long V, int M, int32_t *label,
-                         unsigned long long *offer, int32_t *trig, Control *ctl)
+                         unsigned long long *offer, uint32_t *src_list, Control *ctl)
 {
     const unsigned long long key = ((unsigned long long)(uint32_t)M << 32) | 0xffffffffull;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nA; i += (long long)gridDim.x * blockDim.x) {
@@ -157,7 +178,7 @@ __global__ void k_mark_A(const int64_t *A, long long nA, const uint32_t *isB, lo
             continue;
         }
         label[a] = M;
-        if (atomicExch(offer + a, key) != key) trig[atomicAdd(&ctl->cnt[0].n_trig, 1u)] = (int32_t)a;
+        if (atomicExch(offer + a, key) != key) src_list[hi32(atomicAdd(&ctl->cnt[0].out_cand, 1ull << 32))] = (uint32_t)a;
     }
 }
 
@@ -175,33 +196,41 @@ __device__ void write_row(const Params<W> &P, long long row, long long time, lon
 
 __device__ __forceinline__ void zero_counters(Counters *c)
 {
-    c->n_live = c->launched = c->xkey = 0;
-    c->n_out = c->n_trig = c->arrivals = c->n_active = c->overflow = c->abort = 0;
+    c->out_cand = c->live = c->lau_imp = c->xkey = 0;
+    c->n_active = c->overflow = c->abort = 0;
     c->min_ta = INT_MAX;
 }
 
-__device__ __forceinline__ Counters read_counters(const Counters *c)
+// A snapshot of one pass's counters, read by every CTA after the pass's last barrier.
+struct PassCounts {
+    unsigned int n_out, n_cand, launched, improved, n_active, overflow, abort;
+    unsigned long long n_live, xkey;
+    int min_ta;
+};
+
+__device__ __forceinline__ PassCounts read_counters(const Counters *c)
 {
-    Counters r;
+    PassCounts r;
     const volatile Counters *vc = c;
-    r.n_live = vc->n_live;
-    r.launched = vc->launched;
+    const unsigned long long oc = vc->out_cand, li = vc->lau_imp;
+    r.n_out = lo32(oc);
+    r.n_cand = hi32(oc);
+    r.launched = lo32(li);
+    r.improved = hi32(li);
+    r.n_live = vc->live;
     r.xkey = vc->xkey;
-    r.n_out = vc->n_out;
-    r.n_trig = vc->n_trig;
-    r.arrivals = vc->arrivals;
     r.n_active = vc->n_active;
     r.overflow = vc->overflow;
-    r.min_ta = vc->min_ta;
     r.abort = vc->abort;
+    r.min_ta = vc->min_ta;
     return r;
 }
 
 template <int D, typename W, bool TRACE>
-__global__ void __launch_bounds__(TPB, 2) k_cycle(Params<W> P)
+__global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_cycle(Params<W> P)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileStage &stage = *reinterpret_cast<TileStage *>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     __shared__ uint32_t s_warp[NWARP];
     __shared__ uint32_t s_base[2];
 
@@ -209,15 +238,21 @@ __global__ void __launch_bounds__(TPB, 2) k_cycle(Params<W> P)
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long epoch = 0;
     const int M = P.M;
-    const unsigned int tag0 = *(volatile unsigned int *)&ctl->tag;
     const unsigned long long t_start = globaltimer_ns();
+    uint32_t parity[2] = {0u, 0u};
 
     long long cycle = 0, updates = 0, launched = 0, passes = 0, trace_len = 0, arrivals = 0, improved = 0;
     unsigned int max_pool = 0;
     int Time = 0, status = ST_OK;
     bool feasible = false;
     unsigned long long xkey = 0;
-    int last_buf = 0;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.mbar[0], 1);
+        mbar_init(&sm.mbar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
 
     if (*(volatile int *)&ctl->status_in != 0) {
         status = *(volatile int *)&ctl->status_in;
@@ -232,11 +267,11 @@ __global__ void __launch_bounds__(TPB, 2) k_cycle(Params<W> P)
     {
         // seed: water leaves A at Time 0 along every edge that can raise a label
         LocalStats st{0, 0, 0, 0, INT_MAX};
-        const uint32_t n_seed = min(*(volatile unsigned int *)&ctl->cnt[0].n_trig, P.trig_cap);
-        launch<D, W>(P, 0, n_seed, 0, &ctl->cnt[0], st, stage, s_warp, s_base);
+        const uint32_t n_src = min(hi32(*(volatile unsigned long long *)&ctl->cnt[0].out_cand), P.cand_cap);
+        seed<D, W>(P, n_src, &ctl->cnt[0], st, sm, s_warp, s_base);
         flush_stats(st, &ctl->cnt[0]);
         if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
-        const Counters c = read_counters(&ctl->cnt[0]);
+        const PassCounts c = read_counters(&ctl->cnt[0]);
         launched += (long long)c.launched;
         if (c.overflow) { status = ST_CAPACITY; goto finish; }
         if (c.n_out == 0) {  // nothing can leave A: infeasible
@@ -250,28 +285,30 @@ __global__ void __launch_bounds__(TPB, 2) k_cycle(Params<W> P)
         for (long long pass = 1;; pass++) {
             const int ib = (int)((pass - 1) & 1), ob = ib ^ 1;
             Counters *C = &ctl->cnt[ob];
-            const uint32_t n_in = *(volatile unsigned int *)&ctl->cnt[ib].n_out;
+            const uint32_t n_in = lo32(*(volatile unsigned long long *)&ctl->cnt[ib].out_cand);
             LocalStats sa{0, 0, 0, 0, INT_MAX};
-            sweep<D, W, TRACE>(P, ib, n_in, Tg, C, tag0 + (uint32_t)pass, sa, stage, s_warp, s_base);
+            if (!sweep<D, W, TRACE>(P, ib, n_in, Tg, C, sa, sm, parity, s_warp, s_base)) {
+                status = ST_BARRIER;
+                goto finish;
+            }
             flush_stats(sa, C);
             if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
             if (leader) zero_counters(&ctl->cnt[ib]);  // everyone has read n_in
             if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
             LocalStats sb{0, 0, 0, 0, INT_MAX};
-            const uint32_t n_trig = min(*(volatile unsigned int *)&C->n_trig, P.trig_cap);
-            launch<D, W>(P, ob, n_trig, Tg, C, sb, stage, s_warp, s_base);
+            const uint32_t n_cand = min(hi32(*(volatile unsigned long long *)&C->out_cand), P.cand_cap);
+            launch<D, W, TRACE>(P, ob, n_cand, Tg, C, sb, sm, s_warp, s_base);
             flush_stats(sb, C);
             if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
             passes = pass;
-            last_buf = ob;
 
-            const Counters c = read_counters(C);
+            const PassCounts c = read_counters(C);
             launched += (long long)c.launched;
-            arrivals += (long long)c.arrivals;
-            improved += (long long)c.n_trig;
+            arrivals += (long long)c.n_cand;
+            improved += (long long)c.improved;
             if (c.overflow) { status = ST_CAPACITY; goto finish; }
             if (c.abort) { status = ST_TIMEOUT; goto finish; }
-            if (c.arrivals > 0) {  // a real cycle at time Tg
+            if (c.n_cand > 0) {  // a real cycle at time Tg
                 if (TRACE && leader) write_row(P, cycle, Time, c.n_active, (long long)c.n_live);
                 updates += (long long)c.n_live;
                 cycle++;
@@ -282,11 +319,17 @@ __global__ void __launch_bounds__(TPB, 2) k_cycle(Params<W> P)
                     if (TRACE) {
                         // the terminal cycle's row: count the flows still alive after it
                         LocalStats sc{0, 0, 0, 0, INT_MAX};
-                        sweep<D, W, TRACE>(P, ob, c.n_out, -1, &ctl->cnt[ib], tag0 + (uint32_t)pass + 1u, sc, stage,
-                                           s_warp, s_base);
+                        if (!sweep<D, W, TRACE>(P, ob, c.n_out, -1, &ctl->cnt[ib], sc, sm, parity, s_warp, s_base)) {
+                            status = ST_BARRIER;
+                            goto finish;
+                        }
                         flush_stats(sc, &ctl->cnt[ib]);
                         if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
-                        const Counters cc = read_counters(&ctl->cnt[ib]);
+                        LocalStats sd{0, 0, 0, 0, INT_MAX};
+                        launch<D, W, TRACE>(P, ob, 0, Time, &ctl->cnt[ib], sd, sm, s_warp, s_base);  // count sources
+                        flush_stats(sd, &ctl->cnt[ib]);
+                        if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
+                        const PassCounts cc = read_counters(&ctl->cnt[ib]);
                         if (leader) write_row(P, cycle, Time, cc.n_active, (long long)cc.n_live);
                         trace_len = cycle + 1;
                     }
@@ -330,14 +373,11 @@ finish:
         o[R_PASSES] = passes;
         o[R_MAXPOOL] = max_pool;
         o[R_TRACELEN] = TRACE ? trace_len : 0;
-        o[R_NEXTTAG] = tag0 + passes + 2;
         o[R_ARRIVALS] = arrivals;
         o[R_IMPROVED] = improved;
-        ctl->tag = tag0 + (uint32_t)passes + 2u;
         if (P.result_dev)
             for (int i = 0; i < R_COUNT; i++) P.result_dev[i] = o[i];
     }
-    (void)last_buf;
 }
 
 // ---------------------------------------------------------------- host side
@@ -367,7 +407,7 @@ const void *pick_kernel(int d, int wbytes, bool trace)
     return trace ? pick_kernel_w<uint16_t, true>(d) : pick_kernel_w<uint16_t, false>(d);
 }
 
-constexpr size_t kSmem = sizeof(TileStage);
+constexpr size_t kSmem = sizeof(Smem);
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -385,12 +425,13 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
         off = align_up(off + bytes, 256);
         return o;
     };
+    const int64_t cand_cap = std::max<int64_t>(V, std::min<int64_t>(2 * L->d * V, pool_cap));
     const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
-                 o_stamp = take(V * 4), o_trig = take(V * 4), o_ctl = take(sizeof(Control)),
+                 o_srcbits = take(((V + 31) / 32) * 4), o_cand = take(cand_cap * 4), o_ctl = take(sizeof(Control)),
                  o_trace = take(trace_cap * 24), o_sets = take(sets_cap * 8);
     size_t o_pool[2][3];
     for (int b = 0; b < 2; b++)
-        for (int f = 0; f < 3; f++) o_pool[b][f] = take(pool_cap * 4);
+        for (int f = 0; f < 3; f++) o_pool[b][f] = take((pool_cap + POOL_PAD) * 4);
     void *ws = nullptr;
     cudaError_t e = cudaMalloc(&ws, off);
     if (e != cudaSuccess) {
@@ -404,8 +445,9 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
     L->label = (int32_t *)(b + o_label);
     L->offer = (unsigned long long *)(b + o_offer);
     L->isB = (uint32_t *)(b + o_isB);
-    L->stamp = (uint32_t *)(b + o_stamp);
-    L->trig = (int32_t *)(b + o_trig);
+    L->srcbits = (uint32_t *)(b + o_srcbits);
+    L->cand = (uint32_t *)(b + o_cand);
+    L->cand_cap = cand_cap;
     L->ctl = (Control *)(b + o_ctl);
     L->trace = (long long *)(b + o_trace);
     L->trace_cap = trace_cap;
@@ -417,7 +459,6 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
         L->ta[k] = (int32_t *)(b + o_pool[k][2]);
     }
     L->pool_cap = pool_cap;
-    CSP_CUDA(cudaMemset(L->stamp, 0, V * 4));
     CSP_CUDA(cudaMemset(L->ctl, 0, sizeof(Control)));
     return CSP_OK;
 }
@@ -444,13 +485,13 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
     CSP_CUDA(cudaMemsetAsync(L->label, 0, V * 4, s));
     CSP_CUDA(cudaMemsetAsync(L->offer, 0, V * 8, s));
     CSP_CUDA(cudaMemsetAsync(L->isB, 0, ((V + 31) / 32) * 4, s));
+    if (trace_dev) CSP_CUDA(cudaMemsetAsync(L->srcbits, 0, ((V + 31) / 32) * 4, s));
     const int sms = num_sms(L->device);
-    k_reset<<<sms, 256, 0, s>>>(L->ctl, L->stamp, V);
-    k_tag_fix<<<1, 1, 0, s>>>(L->ctl);
+    k_reset<<<1, 32, 0, s>>>(L->ctl);
     k_mark_B<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nB + 255) / 256)), 256, 0, s>>>(B_dev, nB, L->isB, V,
                                                                                                  L->ctl);
     k_mark_A<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nA + 255) / 256)), 256, 0, s>>>(
-        A_dev, nA, L->isB, V, (int)M, L->label, L->offer, L->trig, L->ctl);
+        A_dev, nA, L->isB, V, (int)M, L->label, L->offer, L->cand, L->ctl);
     CSP_CUDA(cudaGetLastError());
 
     const bool trace = trace_dev != nullptr;
@@ -477,14 +518,15 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         using W = std::remove_cv_t<std::remove_pointer_t<decltype(P.f1)>>;
         P.f1 = (const W *)L->f1;
         P.f2 = (const W *)L->f2;
+        P.rec = (const uint4 *)L->rec;
         P.V = V;
         for (int k = 0; k < 4; k++) P.stride[k] = L->stride[k];
         P.label = L->label;
         P.offer = L->offer;
         P.isB = L->isB;
-        P.stamp = L->stamp;
-        P.trig = L->trig;
-        P.trig_cap = (unsigned int)V;
+        P.srcbits = L->srcbits;
+        P.cand = L->cand;
+        P.cand_cap = (unsigned int)L->cand_cap;
         for (int b = 0; b < 2; b++) {
             P.ed[b] = L->ed[b];
             P.qa[b] = L->qa[b];
@@ -576,8 +618,10 @@ csp_status csp_create_lattice(int d, const int64_t *extents, const void *f1, con
     }
     cudaGetDevice(&L->device);
     const size_t bytes = (size_t)d * V * weight_bytes;
+    L->rec_bytes = record_bytes(d, weight_bytes);
     cudaError_t e = cudaMalloc(&L->f1, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&L->f2, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&L->rec, (size_t)V * L->rec_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         csp_destroy_lattice(L);
@@ -610,10 +654,16 @@ csp_status csp_upload_weights(csp_lattice *L, const void *f1, const void *f2, in
         k_zero_upper_faces<uint8_t><<<blocks, 256, 0, s>>>((uint8_t *)L->f1, (uint8_t *)L->f2, L->V, L->d, st[0], st[1],
                                                            st[2], st[3], n[0], n[1], n[2], n[3]);
         k_flow_bound<uint8_t><<<blocks, 256, 0, s>>>((const uint8_t *)L->f1, L->d * L->V, bound);
+        k_build_records<uint8_t><<<blocks, 256, 0, s>>>((const uint8_t *)L->f1, (const uint8_t *)L->f2, L->V, L->d,
+                                                       st[0], st[1], st[2], st[3], n[0], n[1], n[2], n[3],
+                                                       (unsigned char *)L->rec, L->rec_bytes);
     } else {
         k_zero_upper_faces<uint16_t><<<blocks, 256, 0, s>>>((uint16_t *)L->f1, (uint16_t *)L->f2, L->V, L->d, st[0],
                                                             st[1], st[2], st[3], n[0], n[1], n[2], n[3]);
         k_flow_bound<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t *)L->f1, L->d * L->V, bound);
+        k_build_records<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t *)L->f1, (const uint16_t *)L->f2, L->V, L->d,
+                                                        st[0], st[1], st[2], st[3], n[0], n[1], n[2], n[3],
+                                                        (unsigned char *)L->rec, L->rec_bytes);
     }
     CSP_CUDA(cudaGetLastError());
     CSP_CUDA(cudaMemcpyAsync(&L->flow_bound, bound, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -627,6 +677,7 @@ void csp_destroy_lattice(csp_lattice *L)
     if (!L) return;
     if (L->f1) cudaFree(L->f1);
     if (L->f2) cudaFree(L->f2);
+    if (L->rec) cudaFree(L->rec);
     if (L->ws) cudaFree(L->ws);
     delete L;
 }
@@ -791,18 +842,20 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
         off = align_up(off + bytes, 256);
         return o;
     };
+    const int64_t cand_cap = 2 * d * V;
+    const int rbytes = record_bytes(d, weight_bytes);
     const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
-                 o_trig = take(V * 4), o_ctl = take(sizeof(Control));
+                 o_cand = take(cand_cap * 4), o_rec = take(V * rbytes), o_ctl = take(sizeof(Control));
     const size_t kMinPool = 1024;
     if (off + 2 * 3 * kMinPool * 4 + 3 * 2 * 256 > kStaticBytes) {
         g_last_error = "csp_solve_static: lattice too large for the static workspace (" +
                        std::to_string(kStaticBytes >> 20) + " MiB)";
         return CSP_ERR_INVALID;
     }
-    const size_t pool_cap = std::min<size_t>((kStaticBytes - off - 6 * 256) / 24, 0xF0000000ull);
+    const size_t pool_cap = std::min<size_t>((kStaticBytes - off - 6 * 256) / 24 - POOL_PAD, 0xF0000000ull);
     size_t o_pool[2][3];
     for (int b = 0; b < 2; b++)
-        for (int f = 0; f < 3; f++) o_pool[b][f] = take(pool_cap * 4);
+        for (int f = 0; f < 3; f++) o_pool[b][f] = take((pool_cap + POOL_PAD) * 4);
     if (off > kStaticBytes) {
         g_last_error = "csp_solve_static: workspace layout exceeds the static array";
         return CSP_ERR_INVALID;
@@ -814,7 +867,7 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
     int32_t *label = (int32_t *)(b + o_label);
     unsigned long long *offer = (unsigned long long *)(b + o_offer);
     uint32_t *isB = (uint32_t *)(b + o_isB);
-    int32_t *trig = (int32_t *)(b + o_trig);
+    uint32_t *cand = (uint32_t *)(b + o_cand);
     Control *ctl = (Control *)(b + o_ctl);
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -825,8 +878,7 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
     int dev = 0;
     CSP_CUDA(cudaGetDevice(&dev));
     const int sms = num_sms(dev);
-    k_reset<<<1, 32, 0, s>>>(ctl, nullptr, 0);  // counters; the tag is not used without a trace
-    k_tag_fix<<<1, 1, 0, s>>>(ctl);
+    k_reset<<<1, 32, 0, s>>>(ctl);
     const long long n[4] = {ext[0], ext[1], ext[2], ext[3]};
     const long long stl[4] = {stride[0], stride[1], stride[2], stride[3]};
     const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * 4, (d * V + 255) / 256));
@@ -836,13 +888,23 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
     else
         k_check_upper_faces<uint16_t><<<cblocks, 256, 0, s>>>((const uint16_t *)f1_dev, V, d, stl[0], stl[1], stl[2],
                                                               stl[3], n[0], n[1], n[2], n[3], ctl);
+    const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>(sms * 8, (V + 255) / 256));
+    if (weight_bytes == 1)
+        k_build_records<uint8_t><<<rblocks, 256, 0, s>>>((const uint8_t *)f1_dev, (const uint8_t *)f2_dev, V, d,
+                                                        stl[0], stl[1], stl[2], stl[3], n[0], n[1], n[2], n[3],
+                                                        (unsigned char *)(b + o_rec), rbytes);
+    else
+        k_build_records<uint16_t><<<rblocks, 256, 0, s>>>((const uint16_t *)f1_dev, (const uint16_t *)f2_dev, V, d,
+                                                         stl[0], stl[1], stl[2], stl[3], n[0], n[1], n[2], n[3],
+                                                         (unsigned char *)(b + o_rec), rbytes);
     k_mark_B<<<(int)std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nB + 255) / 256)), 256, 0, s>>>(B_dev, nB, isB,
                                                                                                      V, ctl);
     k_mark_A<<<(int)std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nA + 255) / 256)), 256, 0, s>>>(
-        A_dev, nA, isB, V, (int)M, label, offer, trig, ctl);
+        A_dev, nA, isB, V, (int)M, label, offer, cand, ctl);
     CSP_CUDA(cudaGetLastError());
 
     const void *fn = pick_kernel(d, weight_bytes, false);
+    CSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     int per_sm = 0;
     CSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TPB, kSmem));
     if (per_sm < 1) {
@@ -856,14 +918,15 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
         using W = std::remove_cv_t<std::remove_pointer_t<decltype(P.f1)>>;
         P.f1 = (const W *)f1_dev;
         P.f2 = (const W *)f2_dev;
+        P.rec = (const uint4 *)(b + o_rec);
         P.V = V;
         for (int k = 0; k < 4; k++) P.stride[k] = stride[k];
         P.label = label;
         P.offer = offer;
         P.isB = isB;
-        P.stamp = nullptr;
-        P.trig = trig;
-        P.trig_cap = (unsigned int)V;
+        P.srcbits = nullptr;
+        P.cand = cand;
+        P.cand_cap = (unsigned int)cand_cap;
         for (int q = 0; q < 2; q++) {
             P.ed[q] = (uint32_t *)(b + o_pool[q][0]);
             P.qa[q] = (int32_t *)(b + o_pool[q][1]);

@@ -122,7 +122,8 @@ csp_status csp_solve(csp_lattice *lat, const int64_t *A, int64_t nA, const int64
  * Asynchronous solve with device-resident sets: enqueues the whole solve on opt->stream
  * and returns without waiting.  A_dev, B_dev are device arrays of int64 ids.  The result
  * is written to result_dev (device, 16 int64: status, F1, X, x_src, x_dir, F2, cycles,
- * updates, launched, passes, max_pool, trace_len, (internal), arrivals, improved, 0).  Invalid ids, A and B not
+ * updates, launched, passes, max_pool, trace_len, elapsed_ns, arrivals, improved, 0;
+ * elapsed_ns = device time of the cycle loop, from %globaltimer).  Invalid ids, A and B not
  * disjoint, pool overflow etc. are reported in result_dev[0], not by the return value
  * (which reports only host-side argument errors and launch failures).  trace_dev:
  * nullable device buffer of 3 * trace_cap int64.  The workspace must have been reserved
@@ -162,6 +163,69 @@ csp_status csp_solve_async(csp_lattice *lat, const int64_t *A_dev, int64_t nA, c
 csp_status csp_solve_static(int d, const int64_t *extents, const void *f1_dev, const void *f2_dev,
                             int weight_bytes, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB,
                             int64_t M, int64_t max_cycles, void *stream, int64_t *result_dev);
+
+/* ------------------------------------------------------------------ batched solves
+ *
+ * Many independent instances (each on its own lattice, with its own sets and bound) in
+ * ONE persistent cooperative launch, captured once as a CUDA graph.  A list scheduler
+ * (cost model: cycles x per-cycle latency + updates / rate) gives each instance a group
+ * of CTAs (a power of two) and a start slot; instances never wait for each other.  The
+ * paper solves one instance at a time; this mode and its scheduler are additions.
+ */
+typedef struct {
+    const csp_lattice *lat;   /* the instance's lattice (not owned) */
+    const int64_t *A;         /* host array, nA >= 1 */
+    int64_t nA;
+    const int64_t *B;         /* host array, nB >= 1 */
+    int64_t nB;
+    int64_t M;
+} csp_query;
+
+typedef struct {
+    int32_t ctas;             /* CTAs of the launch; 0 = every co-resident CTA */
+    int32_t max_group;        /* largest CTA group for one instance (power of 2); 0 = 64 */
+    int32_t no_graph;         /* 1 = launch directly instead of through a CUDA graph */
+    int32_t reserved;
+    int64_t pool_capacity;    /* flows per pool buffer per instance; 0 = max(2^16, 6V) capped by the flow bound */
+    int64_t max_cycles;       /* per instance; 0 = no limit */
+} csp_batch_options;
+
+typedef struct csp_batch csp_batch;
+
+/* Allocates every instance's workspace, uploads the sets, plans the schedule and
+ * captures the launch.  All lattices must use the same weight width.  The lattices must
+ * outlive the batch.  Errors: CSP_ERR_INVALID (any query invalid on the host side),
+ * CSP_ERR_OOM, CSP_ERR_CUDA. */
+csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_options *opt, csp_batch **out);
+
+/* Enqueues one run of the whole batch on stream (cudaStream_t or NULL); asynchronous. */
+csp_status csp_batch_run(csp_batch *b, void *stream);
+
+/* Waits for the device and copies the n results (out), per-instance statuses (nullable;
+ * CSP_ERR_CAPACITY means that instance's pool was too small) and the per-instance device
+ * time of the cycle loop in ns (nullable). */
+csp_status csp_batch_results(csp_batch *b, csp_result *out, int32_t *status, int64_t *elapsed_ns);
+
+/* The current schedule: per instance its group size, first CTA, planned start and
+ * estimated duration (us); *ctas = the launch width.  Every pointer is nullable. */
+csp_status csp_batch_schedule(const csp_batch *b, int32_t *group_size, int32_t *first_cta, double *start_us,
+                              double *est_us, int32_t *ctas);
+
+/* Autotuner step: refits the cost model to one measured run (elapsed_ns and results
+ * from csp_batch_results), re-plans the schedule and re-captures the graph. */
+csp_status csp_batch_tune(csp_batch *b, const int64_t *elapsed_ns, const csp_result *res);
+
+/* The cost model the schedule uses (per-cycle latency of a one-CTA group and of a larger
+ * group, us; updates per us per CTA) and the planned makespan (us).  Nullable outputs. */
+csp_status csp_batch_model(const csp_batch *b, double *lat_single_us, double *lat_group_us, double *rate,
+                           double *makespan_us);
+
+void csp_batch_destroy(csp_batch *b);
+
+/* Convenience: create, run, read the results, re-solve any instance whose pool
+ * overflowed with csp_solve (which grows its pool), destroy.  status: nullable, n. */
+csp_status csp_solve_batch(const csp_query *q, int64_t n, const csp_batch_options *opt, csp_result *out,
+                           int32_t *status);
 
 /* Copies the labels left by the last solve (V int32: M - F2 of the best water that has
  * reached each vertex by the final time, 0 if none) to labels_host. */

@@ -7,14 +7,16 @@ nvcc cross-compiles without a GPU; the library is placed next to this file.
 from __future__ import annotations
 
 import os
+import shutil
 import subprocess
 import sys
+import tempfile
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libcsp.so")
-SOURCES = ["csp_solver.cu"]
+SOURCES = ["csp_solver.cu", "csp_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,11 +39,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale(LIB, deps):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+        flags.append("-Xptxas=-v")
+    tmpdir = tempfile.mkdtemp(prefix="csp_build_")
+    objs = []
+    procs = []
+    for src in SOURCES:  # one translation unit per process, compiled in parallel
+        obj = os.path.join(tmpdir, src.replace(".cu", ".o"))
+        objs.append(obj)
+        procs.append(subprocess.Popen([nvcc(), *flags, "-c", "-o", obj, os.path.join(CSRC, src)]))
+    codes = [p.wait() for p in procs]
+    try:
+        if any(codes):
+            raise subprocess.CalledProcessError(max(codes), "nvcc")
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp] + objs)
+    finally:
+        shutil.rmtree(tmpdir, ignore_errors=True)
     os.replace(tmp, LIB)
     return LIB
 

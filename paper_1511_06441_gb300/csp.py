@@ -245,3 +245,135 @@ def solve_static(extents, f1_dev, f2_dev, A_dev, B_dev, M: int, result_dev, *, m
                                   f1_dev.element_size(), _ptr(A_dev), int(A_dev.numel()), _ptr(B_dev),
                                   int(B_dev.numel()), int(M), int(max_cycles), _stream_handle(stream),
                                   _ptr(result_dev)), "csp_solve_static")
+
+
+class CspQuery(ctypes.Structure):
+    _fields_ = [("lat", vp), ("A", i64p), ("nA", i64), ("B", i64p), ("nB", i64), ("M", i64)]
+
+
+class CspBatchOptions(ctypes.Structure):
+    _fields_ = [("ctas", ctypes.c_int32), ("max_group", ctypes.c_int32), ("no_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("pool_capacity", i64), ("max_cycles", i64)]
+
+
+def _batch_api():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        L.csp_batch_create.argtypes = [ctypes.POINTER(CspQuery), i64, ctypes.POINTER(CspBatchOptions),
+                                       ctypes.POINTER(vp)]
+        L.csp_batch_run.argtypes = [vp, vp]
+        L.csp_batch_results.argtypes = [vp, ctypes.POINTER(CspResult), ctypes.POINTER(ctypes.c_int32), i64p]
+        L.csp_batch_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int32)]
+        L.csp_batch_tune.argtypes = [vp, i64p, ctypes.POINTER(CspResult)]
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.csp_batch_model.argtypes = [vp, dp, dp, dp, dp]
+        L.csp_batch_model.restype = ctypes.c_int
+        L.csp_batch_destroy.argtypes = [vp]
+        L.csp_batch_destroy.restype = None
+        L.csp_solve_batch.argtypes = [ctypes.POINTER(CspQuery), i64, ctypes.POINTER(CspBatchOptions),
+                                      ctypes.POINTER(CspResult), ctypes.POINTER(ctypes.c_int32)]
+        for f in ("csp_batch_create", "csp_batch_run", "csp_batch_results", "csp_batch_schedule", "csp_batch_tune",
+                  "csp_solve_batch"):
+            getattr(L, f).restype = ctypes.c_int
+        L._batch_ready = True
+    return L
+
+
+def _queries(items):
+    """items: iterable of (Lattice, A, B, M).  Returns the ctypes array and the kept arrays."""
+    keep = []
+    arr = (CspQuery * len(items))()
+    for i, (lat, A, B, M) in enumerate(items):
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
+        B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
+        keep += [A, B]
+        arr[i] = CspQuery(lat.handle, A.ctypes.data_as(i64p), A.size, B.ctypes.data_as(i64p), B.size, int(M))
+    return arr, keep
+
+
+def _results(res, n, stat=None, el=None):
+    out = []
+    for i in range(n):
+        r = Result(*[int(getattr(res[i], name)) for name, _ in CspResult._fields_])
+        if stat is not None:
+            r.status = int(stat[i])
+        if el is not None:
+            r.elapsed_ns = int(el[i])
+        out.append(r)
+    return out
+
+
+class Batch:
+    """``csp_batch_*``: many instances in one persistent, graph-captured launch."""
+
+    def __init__(self, items, *, ctas: int = 0, max_group: int = 0, no_graph: bool = False, pool_capacity: int = 0,
+                 max_cycles: int = 0):
+        L = _batch_api()
+        self.n = len(items)
+        q, _keep = _queries(items)
+        opt = CspBatchOptions(ctas, max_group, int(no_graph), 0, pool_capacity, max_cycles)
+        h = vp()
+        _check(L.csp_batch_create(q, self.n, ctypes.byref(opt), ctypes.byref(h)), "csp_batch_create")
+        self._h = h
+        self._lattices = [it[0] for it in items]  # the lattices must outlive the batch
+
+    def run(self, stream=None):
+        _check(_batch_api().csp_batch_run(self._h, _stream_handle(stream)), "csp_batch_run")
+
+    def results(self):
+        res = (CspResult * self.n)()
+        stat = (ctypes.c_int32 * self.n)()
+        el = np.zeros(self.n, np.int64)
+        _check(_batch_api().csp_batch_results(self._h, res, stat, el.ctypes.data_as(i64p)), "csp_batch_results")
+        return _results(res, self.n, stat, el)
+
+    def schedule(self):
+        n = self.n
+        g = (ctypes.c_int32 * n)()
+        f = (ctypes.c_int32 * n)()
+        st = (ctypes.c_double * n)()
+        est = (ctypes.c_double * n)()
+        c = ctypes.c_int32(0)
+        _check(_batch_api().csp_batch_schedule(self._h, g, f, st, est, ctypes.byref(c)), "csp_batch_schedule")
+        return {"group": np.array(g[:]), "first_cta": np.array(f[:]), "start_us": np.array(st[:]),
+                "est_us": np.array(est[:]), "ctas": int(c.value)}
+
+    def tune(self, results):
+        el = np.ascontiguousarray(np.array([r.elapsed_ns for r in results], np.int64))
+        res = (CspResult * self.n)()
+        for i, r in enumerate(results):
+            for name, _ in CspResult._fields_:
+                setattr(res[i], name, getattr(r, name))
+        _check(_batch_api().csp_batch_tune(self._h, el.ctypes.data_as(i64p), res), "csp_batch_tune")
+
+    def model(self):
+        v = [ctypes.c_double(0) for _ in range(4)]
+        _check(_batch_api().csp_batch_model(self._h, *[ctypes.byref(x) for x in v]), "csp_batch_model")
+        return {"lat_single_us": v[0].value, "lat_group_us": v[1].value, "rate": v[2].value,
+                "makespan_us": v[3].value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _batch_api().csp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(items, *, ctas: int = 0, max_group: int = 0, no_graph: bool = False, pool_capacity: int = 0,
+                max_cycles: int = 0):
+    """``csp_solve_batch``: one call; instances whose pool overflowed are re-solved alone."""
+    L = _batch_api()
+    q, _keep = _queries(items)
+    n = len(items)
+    opt = CspBatchOptions(ctas, max_group, int(no_graph), 0, pool_capacity, max_cycles)
+    res = (CspResult * n)()
+    stat = (ctypes.c_int32 * n)()
+    _check(L.csp_solve_batch(q, n, ctypes.byref(opt), res, stat), "csp_solve_batch")
+    return _results(res, n, stat)

@@ -42,7 +42,7 @@ enum : int { ST_OK = 0, ST_INVALID = 1, ST_OOM = 2, ST_CUDA = 3, ST_CAPACITY = 4
 // result record (int64): index of each field
 enum : int {
     R_STATUS = 0, R_F1, R_X, R_XSRC, R_XDIR, R_F2, R_CYCLES, R_UPDATES, R_LAUNCHED, R_PASSES,
-    R_MAXPOOL, R_TRACELEN, R_RESERVED, R_ARRIVALS, R_IMPROVED, R_COUNT = 16
+    R_MAXPOOL, R_TRACELEN, R_ELAPSED_NS, R_ARRIVALS, R_IMPROVED, R_COUNT = 16
 };
 
 __host__ __device__ __forceinline__ unsigned int lo32(unsigned long long x) { return (unsigned int)(x & 0xffffffffull); }
@@ -120,7 +120,8 @@ struct Params {
     long long *result_dev;         // nullable mirror of ctl->out
     int M;
     long long max_cycles;
-    unsigned long long budget_ns;  // wall-clock budget of one launch (watchdog)
+    unsigned long long budget_ns;   // wall-clock budget of one launch (watchdog)
+    unsigned long long barrier_ns;  // longest wait at one barrier before giving up
 };
 
 // Dynamic shared memory of the cycle kernel: two input stages filled by bulk copies,
@@ -133,6 +134,13 @@ struct Smem {
     int32_t out_qa[TILE];
     int32_t out_ta[TILE];
     unsigned long long mbar[2];
+};
+
+// The CTAs that cooperate on one solve: the whole grid for a single solve, a slice of
+// it in batched mode.  rank = index of this CTA in the group.
+struct Group {
+    uint32_t rank, size;
+    __device__ __forceinline__ bool leader() const { return rank == 0 && threadIdx.x == 0; }
 };
 
 // ---------------------------------------------------------------- small helpers
@@ -150,7 +158,7 @@ __device__ __forceinline__ int dir_offset(const int (&stride)[4], unsigned r)
 
 __device__ __forceinline__ bool in_set(const uint32_t *bits, uint32_t v)
 {
-    return (__ldg(bits + (v >> 5)) >> (v & 31)) & 1u;
+    return (__ldcg(bits + (v >> 5)) >> (v & 31)) & 1u;
 }
 
 // x code of a flow arriving at dst from direction r (r = direction from dst back to the
@@ -196,19 +204,21 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Grid-wide barrier for a cooperative (co-resident) launch.  Arrivals are counted on one
+// Barrier over the CTAs of a group (all co-resident: cooperative launch).  Arrivals are counted on one
 // word; the last CTA to arrive publishes the new epoch to NRELEASE release words on
 // separate lines, and every CTA polls its own copy (with a short sleep between polls).
 // Spreading the polls keeps the waiting CTAs from saturating one L2 slice while the
-// slowest CTAs are still working.  The wait gives up after ~4 s or 2^26 polls, sets
+// slowest CTAs are still working.  The wait gives up after limit_ns or 2^30 polls, sets
 // ctl->err and returns false; every CTA then leaves the kernel.
-__device__ __forceinline__ bool grid_sync(Control *ctl, unsigned long long &epoch)
+__device__ __forceinline__ bool group_sync(Control *ctl, unsigned long long &epoch, const Group &g,
+                                           unsigned long long limit_ns)
 {
     __shared__ int s_ok;
     __syncthreads();
+    if (g.size == 1) return true;  // one CTA: the block barrier is enough
     if (threadIdx.x == 0) {
         epoch += 1;
-        const unsigned long long target = epoch * gridDim.x;
+        const unsigned long long target = epoch * g.size;
         __threadfence();
         const unsigned long long arrived = atomicAdd(&ctl->bar, 1ull) + 1ull;
         int ok = 1;
@@ -220,7 +230,7 @@ __device__ __forceinline__ bool grid_sync(Control *ctl, unsigned long long &epoc
                 asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&ctl->release[i].epoch), "l"(epoch)
                              : "memory");
         } else {
-            const unsigned long long *word = &ctl->release[blockIdx.x % NRELEASE].epoch;
+            const unsigned long long *word = &ctl->release[g.rank % NRELEASE].epoch;
             const unsigned long long t0 = globaltimer_ns();
             for (unsigned int spin = 0;; ++spin) {
                 unsigned long long seen;
@@ -228,7 +238,7 @@ __device__ __forceinline__ bool grid_sync(Control *ctl, unsigned long long &epoc
                 if (seen >= epoch) break;
                 if ((spin & 63u) == 63u) {
                     if (*(volatile int *)&ctl->err) { ok = 0; break; }
-                    if (spin > (1u << 26) || globaltimer_ns() - t0 > 4000000000ull) {
+                    if (spin > (1u << 30) || globaltimer_ns() - t0 > limit_ns) {
                         atomicExch(&ctl->err, 1);
                         ok = 0;
                         break;
@@ -444,19 +454,19 @@ __device__ __forceinline__ void write_flows(const Params<W> &P, int ob, Counters
 // bit in srcbits (counted by the launch phase).
 // Returns false if a copy wait timed out (ctl->err set).
 template <int D, typename W, bool TRACE>
-__device__ bool sweep(const Params<W> &P, int ib, uint32_t n_in, int Tg, Counters *C, LocalStats &st, Smem &sm,
-                      uint32_t (&parity)[2], uint32_t *s_warp, uint32_t *s_base)
+__device__ bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_in, int Tg, Counters *C, LocalStats &st,
+                      Smem &sm, uint32_t (&parity)[2], uint32_t *s_warp, uint32_t *s_base)
 {
     const int ob = ib ^ 1;
-    const uint32_t G = gridDim.x;
+    const uint32_t G = g.size;
     const uint32_t n_tiles = (n_in + TILE - 1) / TILE;
-    if (threadIdx.x == 0 && blockIdx.x < n_tiles) {
+    if (threadIdx.x == 0 && g.rank < n_tiles) {
         fence_proxy_async_global();  // pool written by ordinary stores in the previous pass
-        issue_tile(P, sm, 0, ib, blockIdx.x, n_in);
-        if (blockIdx.x + G < n_tiles) issue_tile(P, sm, 1, ib, blockIdx.x + G, n_in);
+        issue_tile(P, sm, 0, ib, g.rank, n_in);
+        if (g.rank + G < n_tiles) issue_tile(P, sm, 1, ib, g.rank + G, n_in);
     }
     uint32_t k = 0;
-    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += G, k++) {
+    for (uint32_t tile = g.rank; tile < n_tiles; tile += G, k++) {
         const int s = (int)(k & 1u);
         if (!wait_stage(sm, s, parity[s], P.ctl)) return false;
         parity[s] ^= 1u;
@@ -610,13 +620,13 @@ __device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters 
 // Its loads (offer[v], the edge record, the 2d neighbour labels) are issued together.
 // With TRACE, also counts (and clears) the source bitmap filled by the sweep.
 template <int D, typename W, bool TRACE>
-__device__ void launch(const Params<W> &P, int ob, uint32_t n_cand, int Time, Counters *C, LocalStats &st, Smem &sm,
-                       uint32_t *s_warp, uint32_t *s_base)
+__device__ void launch(const Params<W> &P, const Group &g, int ob, uint32_t n_cand, int Time, Counters *C, LocalStats &st,
+                       Smem &sm, uint32_t *s_warp, uint32_t *s_base)
 {
     const uint32_t V = (uint32_t)P.V;
     if (TRACE) {
         const uint32_t words = (V + 31) / 32;
-        for (uint32_t w = blockIdx.x * TPB + threadIdx.x; w < words; w += gridDim.x * TPB) {
+        for (uint32_t w = g.rank * TPB + threadIdx.x; w < words; w += g.size * TPB) {
             const uint32_t b = __ldcg(P.srcbits + w);
             if (b) {
                 st.active += __popc(b);
@@ -624,7 +634,7 @@ __device__ void launch(const Params<W> &P, int ob, uint32_t n_cand, int Time, Co
             }
         }
     }
-    for (uint32_t base = blockIdx.x * TPB; base < n_cand; base += gridDim.x * TPB) {
+    for (uint32_t base = g.rank * TPB; base < n_cand; base += g.size * TPB) {
         const uint32_t j = base + threadIdx.x;
         uint32_t v = 0, mask = 0;
         int Lv = 0;
@@ -653,11 +663,11 @@ __device__ void launch(const Params<W> &P, int ob, uint32_t n_cand, int Time, Co
 // Seed launch (Algorithm 3): water of quality M leaves every source a in A (listed in
 // cand as plain vertex ids, label M already set) along each edge with M - f2 > Label(w).
 template <int D, typename W>
-__device__ void seed(const Params<W> &P, uint32_t n_src, Counters *C, LocalStats &st, Smem &sm, uint32_t *s_warp,
-                     uint32_t *s_base)
+__device__ void seed(const Params<W> &P, const Group &g, uint32_t n_src, Counters *C, LocalStats &st, Smem &sm,
+                     uint32_t *s_warp, uint32_t *s_base)
 {
     const uint32_t V = (uint32_t)P.V;
-    for (uint32_t base = blockIdx.x * TPB; base < n_src; base += gridDim.x * TPB) {
+    for (uint32_t base = g.rank * TPB; base < n_src; base += g.size * TPB) {
         const uint32_t j = base + threadIdx.x;
         uint32_t v = 0, mask = 0;
         EdgeRecord<W, D> r{};
@@ -670,6 +680,262 @@ __device__ void seed(const Params<W> &P, uint32_t n_src, Counters *C, LocalStats
         }
         emit_flows<W, D>(P, 0, C, v, P.M, r, mask, 0, st, sm, s_warp, s_base);
     }
+}
+
+// ---------------------------------------------------------------- one solve
+
+__device__ __forceinline__ void init_stage_barriers(Smem &sm)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.mbar[0], 1);
+        mbar_init(&sm.mbar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+}
+
+template <typename W>
+__device__ void write_row(const Params<W> &P, long long row, long long time, long long active, long long flows)
+{
+    if (P.trace && row < P.trace_cap) {
+        P.trace[3 * row] = time;
+        P.trace[3 * row + 1] = active;
+        P.trace[3 * row + 2] = flows;
+    }
+}
+
+__device__ __forceinline__ void zero_counters(Counters *c)
+{
+    c->out_cand = c->live = c->lau_imp = c->xkey = 0;
+    c->n_active = c->overflow = c->abort = 0;
+    c->min_ta = INT_MAX;
+}
+
+// A snapshot of one pass's counters, read by every CTA after the pass's last barrier.
+struct PassCounts {
+    unsigned int n_out, n_cand, launched, improved, n_active, overflow, abort;
+    unsigned long long n_live, xkey;
+    int min_ta;
+};
+
+__device__ __forceinline__ PassCounts read_counters(const Counters *c)
+{
+    PassCounts r;
+    const volatile Counters *vc = c;
+    const unsigned long long oc = vc->out_cand, li = vc->lau_imp;
+    r.n_out = lo32(oc);
+    r.n_cand = hi32(oc);
+    r.launched = lo32(li);
+    r.improved = hi32(li);
+    r.n_live = vc->live;
+    r.xkey = vc->xkey;
+    r.n_active = vc->n_active;
+    r.overflow = vc->overflow;
+    r.abort = vc->abort;
+    r.min_ta = vc->min_ta;
+    return r;
+}
+
+// Runs one whole solve (the cycle loop of Algorithm 1) on the CTAs of group g.  The
+// set-up must be complete: labels and offers (M on A, 0 elsewhere), the B bitmap, the
+// distinct sources listed in cand with their count in the high half of cnt[0].out_cand,
+// and fresh counters.  The group leader writes the result record.
+template <int D, typename W, bool TRACE>
+__device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t (&parity)[2], uint32_t *s_warp,
+                          uint32_t *s_base, unsigned long long epoch0 = 0)
+{
+    Control *ctl = P.ctl;
+    const bool leader = g.leader();
+    unsigned long long epoch = epoch0;  // barriers already passed on ctl->bar
+    const int M = P.M;
+    const unsigned long long t_start = globaltimer_ns();
+
+    long long cycle = 0, updates = 0, launched = 0, passes = 0, trace_len = 0, arrivals = 0, improved = 0;
+    unsigned int max_pool = 0;
+    int Time = 0, status = ST_OK;
+    bool feasible = false;
+    unsigned long long xkey = 0;
+
+    if (*(volatile int *)&ctl->status_in != 0) {
+        status = *(volatile int *)&ctl->status_in;
+        goto finish;
+    }
+    if (M <= 0) {  // no walk has F2 < M <= 0
+        trace_len = 1;
+        if (leader) write_row(P, 0, 0, 0, 0);
+        goto finish;
+    }
+
+    {
+        // seed: water leaves A at Time 0 along every edge that can raise a label
+        LocalStats st{0, 0, 0, 0, INT_MAX};
+        const uint32_t n_src = min(hi32(*(volatile unsigned long long *)&ctl->cnt[0].out_cand), P.cand_cap);
+        seed<D, W>(P, g, n_src, &ctl->cnt[0], st, sm, s_warp, s_base);
+        flush_stats(st, &ctl->cnt[0]);
+        if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
+        const PassCounts c = read_counters(&ctl->cnt[0]);
+        launched += (long long)c.launched;
+        if (c.overflow) { status = ST_CAPACITY; goto finish; }
+        if (c.n_out == 0) {  // nothing can leave A: infeasible
+            if (leader) write_row(P, 0, 0, 0, 0);
+            trace_len = 1;
+            goto finish;
+        }
+        max_pool = c.n_out;
+        int Tg = c.min_ta;
+
+        for (long long pass = 1;; pass++) {
+            const int ib = (int)((pass - 1) & 1), ob = ib ^ 1;
+            Counters *C = &ctl->cnt[ob];
+            const uint32_t n_in = lo32(*(volatile unsigned long long *)&ctl->cnt[ib].out_cand);
+            LocalStats sa{0, 0, 0, 0, INT_MAX};
+            if (!sweep<D, W, TRACE>(P, g, ib, n_in, Tg, C, sa, sm, parity, s_warp, s_base)) {
+                status = ST_BARRIER;
+                goto finish;
+            }
+            flush_stats(sa, C);
+            if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
+            if (leader) zero_counters(&ctl->cnt[ib]);  // everyone has read n_in
+            if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
+            LocalStats sb{0, 0, 0, 0, INT_MAX};
+            const uint32_t n_cand = min(hi32(*(volatile unsigned long long *)&C->out_cand), P.cand_cap);
+            launch<D, W, TRACE>(P, g, ob, n_cand, Tg, C, sb, sm, s_warp, s_base);
+            flush_stats(sb, C);
+            if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
+            passes = pass;
+
+            const PassCounts c = read_counters(C);
+            launched += (long long)c.launched;
+            arrivals += (long long)c.n_cand;
+            improved += (long long)c.improved;
+            if (c.overflow) { status = ST_CAPACITY; goto finish; }
+            if (c.abort) { status = ST_TIMEOUT; goto finish; }
+            if (c.n_cand > 0) {  // a real cycle at time Tg
+                if (TRACE && leader) write_row(P, cycle, Time, c.n_active, (long long)c.n_live);
+                updates += (long long)c.n_live;
+                cycle++;
+                Time = Tg;
+                if (c.xkey) {  // a vertex of B improved: F1 = Time (Algorithm 2)
+                    feasible = true;
+                    xkey = c.xkey;
+                    if (TRACE) {
+                        // the terminal cycle's row: count the flows still alive after it
+                        LocalStats sc{0, 0, 0, 0, INT_MAX};
+                        if (!sweep<D, W, TRACE>(P, g, ob, c.n_out, -1, &ctl->cnt[ib], sc, sm, parity, s_warp, s_base)) {
+                            status = ST_BARRIER;
+                            goto finish;
+                        }
+                        flush_stats(sc, &ctl->cnt[ib]);
+                        if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
+                        LocalStats sd{0, 0, 0, 0, INT_MAX};
+                        launch<D, W, TRACE>(P, g, ob, 0, Time, &ctl->cnt[ib], sd, sm, s_warp, s_base);  // count sources
+                        flush_stats(sd, &ctl->cnt[ib]);
+                        if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
+                        const PassCounts cc = read_counters(&ctl->cnt[ib]);
+                        if (leader) write_row(P, cycle, Time, cc.n_active, (long long)cc.n_live);
+                        trace_len = cycle + 1;
+                    }
+                    goto finish;
+                }
+            } else if (c.n_live == 0) {  // the pool held no live flow: infeasible
+                if (TRACE && leader) write_row(P, cycle, Time, 0, 0);
+                trace_len = cycle + 1;
+                goto finish;
+            }
+            if (c.n_out == 0) {  // no flow left after a cycle: infeasible
+                if (TRACE && leader) write_row(P, cycle, Time, 0, 0);
+                trace_len = cycle + 1;
+                goto finish;
+            }
+            max_pool = max(max_pool, c.n_out);
+            Tg = c.min_ta;
+            if (P.max_cycles > 0 && cycle >= P.max_cycles) { status = ST_TIMEOUT; goto finish; }
+            if (Tg >= TIME_LIMIT) { status = ST_CAPACITY; goto finish; }
+        }
+    }
+
+finish:
+    if (leader) {
+        long long *o = ctl->out;
+        for (int i = 0; i < R_COUNT; i++) o[i] = -1;
+        o[R_STATUS] = status;
+        if (status == ST_OK && feasible) {
+            const uint32_t X = 0xffffffffu - (uint32_t)(xkey & 0xffffffffu);
+            const int LX = (int)(xkey >> 32);
+            const uint32_t code = 0xffffffffu - (uint32_t)(__ldcg(P.offer + X) & 0xffffffffu);
+            o[R_F1] = Time;
+            o[R_X] = X;
+            o[R_XSRC] = code >> 3;
+            o[R_XDIR] = code & 7u;
+            o[R_F2] = (long long)M - LX;
+        }
+        o[R_CYCLES] = cycle;
+        o[R_UPDATES] = updates;
+        o[R_LAUNCHED] = launched;
+        o[R_PASSES] = passes;
+        o[R_MAXPOOL] = max_pool;
+        o[R_TRACELEN] = TRACE ? trace_len : 0;
+        o[R_ARRIVALS] = arrivals;
+        o[R_IMPROVED] = improved;
+        o[R_ELAPSED_NS] = (long long)(globaltimer_ns() - t_start);
+        if (P.result_dev)
+            for (int i = 0; i < R_COUNT; i++) P.result_dev[i] = o[i];
+    }
+}
+
+// ---------------------------------------------------------------- set-up inside a kernel
+
+// Initialization (Algorithm 3) by the CTAs of group g, for solves started inside a
+// persistent kernel: labels and offers cleared, B marked, Label(a) = M on A (the offer
+// word mirrors it) and the distinct sources listed in cand for the seed launch.  Invalid
+// ids or A and B overlapping set ctl->status_in.  Returns false if a barrier failed.
+template <typename W>
+__device__ bool group_setup(const Params<W> &P, const Group &g, const int64_t *A, long long nA, const int64_t *B,
+                            long long nB, unsigned long long &epoch)
+{
+    Control *ctl = P.ctl;
+    const long long V = P.V;
+    const long long t0 = (long long)g.rank * TPB + threadIdx.x, step = (long long)g.size * TPB;
+    for (long long i = t0; i < V; i += step) {
+        P.label[i] = 0;
+        P.offer[i] = 0ull;
+    }
+    for (long long i = t0; i < (V + 31) / 32; i += step) const_cast<uint32_t *>(P.isB)[i] = 0u;
+    if (g.leader()) {
+        ctl->status_in = 0;
+        for (int b = 0; b < 2; b++) {
+            Counters &c = ctl->cnt[b];
+            c.out_cand = c.live = c.lau_imp = c.xkey = 0;
+            c.n_active = c.overflow = c.abort = 0;
+            c.min_ta = INT_MAX;
+        }
+    }
+    if (!group_sync(ctl, epoch, g, P.barrier_ns)) return false;
+    for (long long i = t0; i < nB; i += step) {
+        const long long b = B[i];
+        if (b < 0 || b >= V) atomicExch(&ctl->status_in, ST_INVALID);
+        else atomicOr(const_cast<uint32_t *>(P.isB) + (b >> 5), 1u << (b & 31));
+    }
+    if (!group_sync(ctl, epoch, g, P.barrier_ns)) return false;
+    const unsigned long long key = ((unsigned long long)(uint32_t)P.M << 32) | 0xffffffffull;
+    for (long long i = t0; i < nA; i += step) {
+        const long long a = A[i];
+        if (a < 0 || a >= V) {
+            atomicExch(&ctl->status_in, ST_INVALID);
+            continue;
+        }
+        if ((__ldcg(P.isB + (a >> 5)) >> (a & 31)) & 1u) {
+            atomicExch(&ctl->status_in, ST_INVALID);  // A and B must be disjoint
+            continue;
+        }
+        P.label[a] = P.M;
+        if (atomicExch(P.offer + a, key) != key) {
+            const unsigned int slot = hi32(atomicAdd(&ctl->cnt[0].out_cand, 1ull << 32));
+            if (slot < P.cand_cap) P.cand[slot] = (uint32_t)a;
+            else atomicExch(&ctl->status_in, ST_CAPACITY);
+        }
+    }
+    return group_sync(ctl, epoch, g, P.barrier_ns);
 }
 
 }  // namespace csp

@@ -1,0 +1,55 @@
+// Host-side definitions shared by the translation units of libcsp (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "csp.h"
+#include "csp_device.cuh"
+
+// Records the text of a failed CUDA call (csp_last_error) and maps it to a status.
+csp_status cuda_fail(cudaError_t e, const char *what);
+void set_error(const std::string &msg);
+extern thread_local std::string g_last_error;
+
+#define CSP_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+inline int record_bytes(int d, int wbytes) { return wbytes * 4 * d <= 16 ? 16 : 32; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct csp_lattice {
+    int d = 0;
+    int wbytes = 1;
+    int64_t ext[4] = {1, 1, 1, 1};
+    int stride[4] = {0, 0, 0, 0};
+    int64_t V = 0;
+    int device = 0;
+    void *f1 = nullptr, *f2 = nullptr;  // device [d][V]
+    void *rec = nullptr;                // device per-vertex edge records
+    int rec_bytes = 16;
+    unsigned long long flow_bound = 0;  // sum of f1 over directed edges: max flows alive
+    // workspace of csp_solve / csp_solve_async
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t pool_cap = 0;
+    int32_t *label = nullptr;
+    unsigned long long *offer = nullptr;
+    uint32_t *isB = nullptr, *srcbits = nullptr;
+    uint32_t *cand = nullptr;
+    int64_t cand_cap = 0;
+    uint32_t *ed[2] = {nullptr, nullptr};
+    int32_t *qa[2] = {nullptr, nullptr}, *ta[2] = {nullptr, nullptr};
+    csp::Control *ctl = nullptr;
+    long long *trace = nullptr;
+    int64_t trace_cap = 0;
+    int64_t *sets = nullptr;  // device copies of A and B
+    int64_t sets_cap = 0;
+};
+
+int num_sms(int device);

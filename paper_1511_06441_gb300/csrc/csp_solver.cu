@@ -28,10 +28,9 @@
 
 #include "csp.h"
 #include "csp_device.cuh"
+#include "csp_internal.h"
 
 using namespace csp;
-
-namespace {
 
 thread_local std::string g_last_error;
 
@@ -41,42 +40,7 @@ csp_status cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? CSP_ERR_OOM : CSP_ERR_CUDA;
 }
 
-#define CSP_CUDA(call)                                    \
-    do {                                                  \
-        cudaError_t e_ = (call);                          \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-    } while (0)
-
-}  // namespace
-
-struct csp_lattice {
-    int d = 0;
-    int wbytes = 1;
-    int64_t ext[4] = {1, 1, 1, 1};
-    int stride[4] = {0, 0, 0, 0};
-    int64_t V = 0;
-    int device = 0;
-    void *f1 = nullptr, *f2 = nullptr;  // device [d][V]
-    void *rec = nullptr;                // device per-vertex edge records
-    int rec_bytes = 16;
-    unsigned long long flow_bound = 0;  // sum of f1 over directed edges: max flows alive
-    // workspace
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-    int64_t pool_cap = 0;
-    int32_t *label = nullptr;
-    unsigned long long *offer = nullptr;
-    uint32_t *isB = nullptr, *srcbits = nullptr;
-    uint32_t *cand = nullptr;
-    int64_t cand_cap = 0;
-    uint32_t *ed[2] = {nullptr, nullptr};
-    int32_t *qa[2] = {nullptr, nullptr}, *ta[2] = {nullptr, nullptr};
-    Control *ctl = nullptr;
-    long long *trace = nullptr;
-    int64_t trace_cap = 0;
-    int64_t *sets = nullptr;  // device copies of A and B
-    int64_t sets_cap = 0;
-};
+void set_error(const std::string &msg) { g_last_error = msg; }
 
 // ---------------------------------------------------------------- set-up kernels
 
@@ -121,7 +85,6 @@ __global__ void k_build_records(const W *f1, const W *f2, long long V, int d, lo
     }
 }
 
-int record_bytes(int d, int wbytes) { return wbytes * 4 * d <= 16 ? 16 : 32; }
 
 template <typename W>
 __global__ void k_flow_bound(const W *f1, long long n, unsigned long long *out)
@@ -184,48 +147,6 @@ __global__ void k_mark_A(const int64_t *A, long long nA, const uint32_t *isB, lo
 
 // ---------------------------------------------------------------- the persistent kernel
 
-template <typename W>
-__device__ void write_row(const Params<W> &P, long long row, long long time, long long active, long long flows)
-{
-    if (P.trace && row < P.trace_cap) {
-        P.trace[3 * row] = time;
-        P.trace[3 * row + 1] = active;
-        P.trace[3 * row + 2] = flows;
-    }
-}
-
-__device__ __forceinline__ void zero_counters(Counters *c)
-{
-    c->out_cand = c->live = c->lau_imp = c->xkey = 0;
-    c->n_active = c->overflow = c->abort = 0;
-    c->min_ta = INT_MAX;
-}
-
-// A snapshot of one pass's counters, read by every CTA after the pass's last barrier.
-struct PassCounts {
-    unsigned int n_out, n_cand, launched, improved, n_active, overflow, abort;
-    unsigned long long n_live, xkey;
-    int min_ta;
-};
-
-__device__ __forceinline__ PassCounts read_counters(const Counters *c)
-{
-    PassCounts r;
-    const volatile Counters *vc = c;
-    const unsigned long long oc = vc->out_cand, li = vc->lau_imp;
-    r.n_out = lo32(oc);
-    r.n_cand = hi32(oc);
-    r.launched = lo32(li);
-    r.improved = hi32(li);
-    r.n_live = vc->live;
-    r.xkey = vc->xkey;
-    r.n_active = vc->n_active;
-    r.overflow = vc->overflow;
-    r.abort = vc->abort;
-    r.min_ta = vc->min_ta;
-    return r;
-}
-
 template <int D, typename W, bool TRACE>
 __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_cycle(Params<W> P)
 {
@@ -233,154 +154,19 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_cycle(Params<W> P)
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     __shared__ uint32_t s_warp[NWARP];
     __shared__ uint32_t s_base[2];
-
-    Control *ctl = P.ctl;
-    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-    unsigned long long epoch = 0;
-    const int M = P.M;
-    const unsigned long long t_start = globaltimer_ns();
+    init_stage_barriers(sm);
     uint32_t parity[2] = {0u, 0u};
-
-    long long cycle = 0, updates = 0, launched = 0, passes = 0, trace_len = 0, arrivals = 0, improved = 0;
-    unsigned int max_pool = 0;
-    int Time = 0, status = ST_OK;
-    bool feasible = false;
-    unsigned long long xkey = 0;
-
-    if (threadIdx.x == 0) {
-        mbar_init(&sm.mbar[0], 1);
-        mbar_init(&sm.mbar[1], 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-
-    if (*(volatile int *)&ctl->status_in != 0) {
-        status = *(volatile int *)&ctl->status_in;
-        goto finish;
-    }
-    if (M <= 0) {  // no walk has F2 < M <= 0
-        trace_len = 1;
-        if (leader) write_row(P, 0, 0, 0, 0);
-        goto finish;
-    }
-
-    {
-        // seed: water leaves A at Time 0 along every edge that can raise a label
-        LocalStats st{0, 0, 0, 0, INT_MAX};
-        const uint32_t n_src = min(hi32(*(volatile unsigned long long *)&ctl->cnt[0].out_cand), P.cand_cap);
-        seed<D, W>(P, n_src, &ctl->cnt[0], st, sm, s_warp, s_base);
-        flush_stats(st, &ctl->cnt[0]);
-        if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
-        const PassCounts c = read_counters(&ctl->cnt[0]);
-        launched += (long long)c.launched;
-        if (c.overflow) { status = ST_CAPACITY; goto finish; }
-        if (c.n_out == 0) {  // nothing can leave A: infeasible
-            if (leader) write_row(P, 0, 0, 0, 0);
-            trace_len = 1;
-            goto finish;
-        }
-        max_pool = c.n_out;
-        int Tg = c.min_ta;
-
-        for (long long pass = 1;; pass++) {
-            const int ib = (int)((pass - 1) & 1), ob = ib ^ 1;
-            Counters *C = &ctl->cnt[ob];
-            const uint32_t n_in = lo32(*(volatile unsigned long long *)&ctl->cnt[ib].out_cand);
-            LocalStats sa{0, 0, 0, 0, INT_MAX};
-            if (!sweep<D, W, TRACE>(P, ib, n_in, Tg, C, sa, sm, parity, s_warp, s_base)) {
-                status = ST_BARRIER;
-                goto finish;
-            }
-            flush_stats(sa, C);
-            if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
-            if (leader) zero_counters(&ctl->cnt[ib]);  // everyone has read n_in
-            if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
-            LocalStats sb{0, 0, 0, 0, INT_MAX};
-            const uint32_t n_cand = min(hi32(*(volatile unsigned long long *)&C->out_cand), P.cand_cap);
-            launch<D, W, TRACE>(P, ob, n_cand, Tg, C, sb, sm, s_warp, s_base);
-            flush_stats(sb, C);
-            if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
-            passes = pass;
-
-            const PassCounts c = read_counters(C);
-            launched += (long long)c.launched;
-            arrivals += (long long)c.n_cand;
-            improved += (long long)c.improved;
-            if (c.overflow) { status = ST_CAPACITY; goto finish; }
-            if (c.abort) { status = ST_TIMEOUT; goto finish; }
-            if (c.n_cand > 0) {  // a real cycle at time Tg
-                if (TRACE && leader) write_row(P, cycle, Time, c.n_active, (long long)c.n_live);
-                updates += (long long)c.n_live;
-                cycle++;
-                Time = Tg;
-                if (c.xkey) {  // a vertex of B improved: F1 = Time (Algorithm 2)
-                    feasible = true;
-                    xkey = c.xkey;
-                    if (TRACE) {
-                        // the terminal cycle's row: count the flows still alive after it
-                        LocalStats sc{0, 0, 0, 0, INT_MAX};
-                        if (!sweep<D, W, TRACE>(P, ob, c.n_out, -1, &ctl->cnt[ib], sc, sm, parity, s_warp, s_base)) {
-                            status = ST_BARRIER;
-                            goto finish;
-                        }
-                        flush_stats(sc, &ctl->cnt[ib]);
-                        if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
-                        LocalStats sd{0, 0, 0, 0, INT_MAX};
-                        launch<D, W, TRACE>(P, ob, 0, Time, &ctl->cnt[ib], sd, sm, s_warp, s_base);  // count sources
-                        flush_stats(sd, &ctl->cnt[ib]);
-                        if (!grid_sync(ctl, epoch)) { status = ST_BARRIER; goto finish; }
-                        const PassCounts cc = read_counters(&ctl->cnt[ib]);
-                        if (leader) write_row(P, cycle, Time, cc.n_active, (long long)cc.n_live);
-                        trace_len = cycle + 1;
-                    }
-                    goto finish;
-                }
-            } else if (c.n_live == 0) {  // the pool held no live flow: infeasible
-                if (TRACE && leader) write_row(P, cycle, Time, 0, 0);
-                trace_len = cycle + 1;
-                goto finish;
-            }
-            if (c.n_out == 0) {  // no flow left after a cycle: infeasible
-                if (TRACE && leader) write_row(P, cycle, Time, 0, 0);
-                trace_len = cycle + 1;
-                goto finish;
-            }
-            max_pool = max(max_pool, c.n_out);
-            Tg = c.min_ta;
-            if (P.max_cycles > 0 && cycle >= P.max_cycles) { status = ST_TIMEOUT; goto finish; }
-            if (Tg >= TIME_LIMIT) { status = ST_CAPACITY; goto finish; }
-        }
-    }
-
-finish:
-    if (leader) {
-        long long *o = ctl->out;
-        for (int i = 0; i < R_COUNT; i++) o[i] = -1;
-        o[R_STATUS] = status;
-        if (status == ST_OK && feasible) {
-            const uint32_t X = 0xffffffffu - (uint32_t)(xkey & 0xffffffffu);
-            const int LX = (int)(xkey >> 32);
-            const uint32_t code = 0xffffffffu - (uint32_t)(__ldcg(P.offer + X) & 0xffffffffu);
-            o[R_F1] = Time;
-            o[R_X] = X;
-            o[R_XSRC] = code >> 3;
-            o[R_XDIR] = code & 7u;
-            o[R_F2] = (long long)M - LX;
-        }
-        o[R_CYCLES] = cycle;
-        o[R_UPDATES] = updates;
-        o[R_LAUNCHED] = launched;
-        o[R_PASSES] = passes;
-        o[R_MAXPOOL] = max_pool;
-        o[R_TRACELEN] = TRACE ? trace_len : 0;
-        o[R_ARRIVALS] = arrivals;
-        o[R_IMPROVED] = improved;
-        if (P.result_dev)
-            for (int i = 0; i < R_COUNT; i++) P.result_dev[i] = o[i];
-    }
+    run_solve<D, W, TRACE>(P, Group{blockIdx.x, gridDim.x}, sm, parity, s_warp, s_base);
 }
 
 // ---------------------------------------------------------------- host side
+
+int num_sms(int device)
+{
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+    return n > 0 ? n : 1;
+}
 
 namespace {
 
@@ -409,7 +195,6 @@ const void *pick_kernel(int d, int wbytes, bool trace)
 
 constexpr size_t kSmem = sizeof(Smem);
 
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
 {
@@ -469,12 +254,6 @@ int64_t default_pool_cap(const csp_lattice *L)
     return (int64_t)std::min<unsigned long long>((unsigned long long)want, std::max(L->flow_bound, 1024ull));
 }
 
-int num_sms(int device)
-{
-    int n = 0;
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
-    return n > 0 ? n : 1;
-}
 
 // Enqueues one solve (set-up kernels + persistent kernel) on stream s.
 csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB, int64_t M,
@@ -539,7 +318,8 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         P.result_dev = (long long *)result_dev;
         P.M = (int)M;
         P.max_cycles = opt ? opt->max_cycles : 0;
-        P.budget_ns = 120ull * 1000000000ull;  // no single solve is expected to take minutes
+        P.budget_ns = 120ull * 1000000000ull;
+        P.barrier_ns = 4000000000ull;  // no single solve is expected to take minutes
     };
     void *args[1];
     if (L->wbytes == 1) {
@@ -940,6 +720,7 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
         P.M = (int)M;
         P.max_cycles = max_cycles > 0 ? max_cycles : 0;
         P.budget_ns = 120ull * 1000000000ull;
+        P.barrier_ns = 4000000000ull;
     };
     void *args[1];
     if (weight_bytes == 1) {

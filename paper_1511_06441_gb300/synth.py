@@ -112,10 +112,10 @@ def vertex_id(c: np.ndarray, extents: Sequence[int]) -> np.ndarray:
 
 def face(extents: Sequence[int], k: int, c: int) -> np.ndarray:
     """All vertex ids with coordinate ``k`` equal to ``c`` (ascending)."""
-    V = num_vertices(extents)
-    v = np.arange(V, dtype=np.int64)
     st = strides(extents)
-    return v[(v // st[k]) % extents[k] == c]
+    lo = np.arange(st[k], dtype=np.int64)                       # coordinates below k
+    hi = np.arange(num_vertices(extents) // (st[k] * extents[k]), dtype=np.int64) * st[k] * extents[k]
+    return (hi[:, None] + c * st[k] + lo[None, :]).reshape(-1)
 
 
 def upper_face_mask(extents: Sequence[int]) -> np.ndarray:
@@ -150,10 +150,54 @@ class Instance:
         return self.f1.dtype.itemsize
 
 
+_fast = None
+
+
+def _fast_lib():
+    """The C fill routines (synth_fill.c), compiled on first use; None if no compiler."""
+    global _fast
+    if _fast is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src, lib = os.path.join(here, "synth_fill.c"), os.path.join(here, "libsynth_fill.so")
+        try:
+            if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+                tmp = lib + f".tmp{os.getpid()}"
+                subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src])
+                os.replace(tmp, lib)
+            L = ctypes.CDLL(lib)
+            L.synth_fill_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int]
+            L.synth_upper_face_mask.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+            _fast = L
+        except Exception:
+            _fast = False
+    return _fast or None
+
+
 def uniform_weights(extents: Sequence[int], lo: int, hi: int, seed: int,
-                    dtype=np.uint8, stream_base: int = 0):
-    """i.i.d. uniform integer travel times and weights in ``[lo, hi]``; upper faces zeroed."""
+                    dtype=np.uint8, stream_base: int = 0, use_c: bool = True):
+    """i.i.d. uniform integer travel times and weights in ``[lo, hi]``; upper faces zeroed.
+
+    ``use_c`` selects the C fill (same SplitMix64 definition, much faster); the numpy
+    path is the reference it is tested against."""
     d, V = len(extents), num_vertices(extents)
+    L = _fast_lib() if use_c else None
+    if L is not None:
+        ext = np.ascontiguousarray(np.asarray(extents, dtype=np.int64))
+        up = np.empty(d * V, np.uint8)
+        L.synth_upper_face_mask(d, ext.ctypes.data, up.ctypes.data)
+        dt = np.dtype(dtype)
+        out = []
+        for stream in (S_F1, S_F2):
+            a = np.empty(d * V, dt)
+            L.synth_fill_uniform(seed, stream_base + stream, d * V, 0, lo, hi, up.ctypes.data, a.ctypes.data,
+                                 dt.itemsize)
+            out.append(a.reshape(d, V))
+        return out[0], out[1]
     f1 = uniform_int(seed, stream_base + S_F1, d * V, lo, hi).reshape(d, V)
     f2 = uniform_int(seed, stream_base + S_F2, d * V, lo, hi).reshape(d, V)
     up = upper_face_mask(extents)

@@ -74,3 +74,19 @@ def test_batch_and_queries():
         assert 1 <= len(q.A) <= 64 and len(set(q.A.tolist())) == len(q.A)
         assert not set(q.A.tolist()) & set(q.B.tolist())
         assert 200 <= q.M <= 2000
+
+
+def test_c_fill_equals_numpy_definition():
+    for ext, lo, hi, dt in (([7, 5, 3], 1, 16, np.uint8), ([33, 17], 0, 300, np.uint16), ([4, 3, 3, 2], 1, 20, np.uint8)):
+        a1, a2 = synth.uniform_weights(ext, lo, hi, 11, dtype=dt, use_c=True)
+        b1, b2 = synth.uniform_weights(ext, lo, hi, 11, dtype=dt, use_c=False)
+        np.testing.assert_array_equal(a1, b1)
+        np.testing.assert_array_equal(a2, b2)
+
+
+def test_face_matches_coordinates():
+    ext = [5, 4, 3]
+    for k in range(3):
+        for c in (0, ext[k] - 1):
+            want = np.nonzero(synth.coords(np.arange(60), ext)[:, k] == c)[0]
+            np.testing.assert_array_equal(synth.face(ext, k, c), want)

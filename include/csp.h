@@ -227,6 +227,21 @@ void csp_batch_destroy(csp_batch *b);
 csp_status csp_solve_batch(const csp_query *q, int64_t n, const csp_batch_options *opt, csp_result *out,
                            int32_t *status);
 
+/*
+ * The minimizing path by repeated application of the method (Section 1 of the paper):
+ * after a solve gives X, x = (Y -> X) and F2, solve again on G' with A' = A, B' = {Y},
+ * M' = F2 - f2(x) + 1 and V' = V minus (B and the path vertices found so far); each step
+ * yields the next vertex back, until Y is in A.  (The paper writes B' = {X} and
+ * M' = F2 - f2(x); with the strict bound F2 < M that would exclude the sub-path itself.)
+ *   res    nullable: the result of csp_solve for (A, B, M); solved here when NULL.
+ *   path   host buffer of cap int64: vertex ids from the A end to X.
+ *   len    receives the number of vertices (0 if no path has F2 < M).  If *len > cap the
+ *          call returns CSP_ERR_CAPACITY and writes nothing.
+ * One full solve per path vertex; blocks until done.
+ */
+csp_status csp_reconstruct_path(csp_lattice *lat, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB,
+                                int64_t M, const csp_result *res, int64_t *path, int64_t cap, int64_t *len);
+
 /* Copies the labels left by the last solve (V int32: M - F2 of the best water that has
  * reached each vertex by the final time, 0 if none) to labels_host. */
 csp_status csp_get_labels(csp_lattice *lat, int32_t *labels_host);

@@ -51,7 +51,8 @@ def _load():
             i32p = ctypes.POINTER(ctypes.c_int32)
             lib.oracle_cycle.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, i64p,
-                                         i64p, ctypes.c_int64, i64p, ctypes.c_int64, i64p, i64p, i64p]
+                                         i64p, ctypes.c_int64, i64p, ctypes.c_int64, i64p, i64p, i64p,
+                                         ctypes.c_void_p]
             lib.oracle_pareto.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
                                           ctypes.c_int64, ctypes.c_int64, i64p]
             lib.oracle_lexmin.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
@@ -105,7 +106,7 @@ def _common(extents, f1, f2, A, B):
 
 def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 << 62,
           trace: bool = True, labels: bool = False, snap_time: Optional[int] = None,
-          allow_timeout: bool = False) -> Result:
+          allow_timeout: bool = False, removed=None) -> Result:
     """O1: the paper's cycle loop.  Raises :class:`OracleError` on a non-OK status.
 
     With ``allow_timeout`` a run stopped by ``max_cycles`` returns its work counts
@@ -114,6 +115,10 @@ def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 <
     lib = _load()
     ext, f1, f2, A, B = _common(extents, f1, f2, A, B)
     V = int(np.prod(ext))
+    rem = None
+    if removed is not None:
+        rem = np.zeros(V, np.uint8)
+        rem[np.asarray(removed, dtype=np.int64)] = 1
     res = np.zeros(8, np.int64)
     cap = 1 << 12
     while True:
@@ -126,7 +131,8 @@ def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 <
                               int(M), int(max_cycles), _p64(res), _p64(tr), cap if trace else 0, _p64(tl),
                               -1 if snap_time is None else int(snap_time),
                               _p64(snap) if snap is not None else None, _p64(sl),
-                              _p64(lab) if lab is not None else None)
+                              _p64(lab) if lab is not None else None,
+                              rem.ctypes.data if rem is not None else None)
         if rc == TIMEOUT and allow_timeout:
             res[:5] = -2
         elif rc != OK:
@@ -138,6 +144,43 @@ def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 <
                   trace=tr[: 3 * int(tl[0])].reshape(-1, 3) if trace else None,
                   labels=lab,
                   snapshot=snap[: int(sl[0])] if snap is not None else None)
+
+
+def edge_weight(extents: Sequence[int], f1, f2, v: int, direction: int):
+    """(f1, f2) of the edge leaving v in direction 2k + s (s = 1: towards -e_k)."""
+    ext = [int(n) for n in extents]
+    d, V = len(ext), int(np.prod(ext))
+    k, s = direction // 2, direction % 2
+    stride = int(np.prod(ext[:k]))
+    slot = k * V + (v - stride if s else v)
+    return int(np.asarray(f1).reshape(-1)[slot]), int(np.asarray(f2).reshape(-1)[slot])
+
+
+def reconstruct(extents: Sequence[int], f1, f2, A, B, M: int, first: Optional[Result] = None,
+                max_steps: int = 1 << 30):
+    """The minimizing path by repeated application (Section 1), with the reading
+    B' = {Y}, M' = F2 - f2(x) + 1, V' = V minus (B and the path vertices found so far),
+    A' = A, until Y is in A.  Returns (path from A to X, per-step results), or
+    (None, [first]) when infeasible.  Each step is a full O1 solve."""
+    r = first if first is not None else cycle(extents, f1, f2, A, B, M, trace=False)
+    steps = [r]
+    if r.F1 < 0:
+        return None, steps
+    Aset = set(int(a) for a in np.asarray(A).reshape(-1))
+    Bset = set(int(b) for b in np.asarray(B).reshape(-1))
+    path = [r.X]
+    F2, Y, xd, X = r.F2, r.x_src, r.x_dir, r.X
+    while Y not in Aset and len(steps) <= max_steps:
+        _, w2 = edge_weight(extents, f1, f2, Y, xd)
+        removed = sorted(Bset | set(path))
+        r = cycle(extents, f1, f2, A, [Y], F2 - w2 + 1, trace=False, removed=removed)
+        steps.append(r)
+        if r.F1 < 0 or r.X != Y:
+            raise RuntimeError("repeated application lost the path")
+        path.append(Y)
+        F2, Y, xd = r.F2, r.x_src, r.x_dir
+    path.append(Y)
+    return path[::-1], steps
 
 
 def pareto(extents: Sequence[int], f1, f2, A, B, M: int) -> Result:

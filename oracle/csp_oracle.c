@@ -58,6 +58,7 @@ typedef struct {
     int d;
     int64_t ext[4], stride[4], V;
     const int32_t *f1, *f2;
+    const unsigned char *removed; /* nullable: vertices not in the graph (V' of Section 1) */
 } lattice_t;
 
 static int lattice_init(lattice_t *L, int d, const int64_t *ext, const int32_t *f1, const int32_t *f2)
@@ -73,6 +74,7 @@ static int lattice_init(lattice_t *L, int d, const int64_t *ext, const int32_t *
     }
     L->f1 = f1;
     L->f2 = f2;
+    L->removed = NULL;
     return OR_OK;
 }
 
@@ -93,6 +95,7 @@ static int64_t neighbour(const lattice_t *L, int64_t v, int dir, int64_t *time, 
         slot = (int64_t)k * L->V + u;
     }
     if (L->f1[slot] <= 0) return -1;
+    if (L->removed && (L->removed[u] || L->removed[v])) return -1;
     *time = L->f1[slot];
     *weight = L->f2[slot];
     return u;
@@ -202,17 +205,20 @@ static int cmp_i64(const void *x, const void *y)
  * state after initialisation; *trace_len is the number of rows produced (it may exceed
  * trace_cap, then only trace_cap rows are written).  If snap is not NULL it receives the
  * active vertices (ascending) at the end of the last cycle whose Time <= snap_time.
- * labels_out (nullable, V entries) receives the labels at termination.
+ * labels_out (nullable, V entries) receives the labels at termination.  removed
+ * (nullable, V bytes) lists vertices that are not part of the graph; A and B must avoid them.
  */
 int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2,
                  const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
                  int64_t max_cycles, int64_t *res,
                  int64_t *trace, int64_t trace_cap, int64_t *trace_len,
-                 int64_t snap_time, int64_t *snap, int64_t *snap_len, int64_t *labels_out)
+                 int64_t snap_time, int64_t *snap, int64_t *snap_len, int64_t *labels_out,
+                 const unsigned char *removed)
 {
     lattice_t L;
     int rc = lattice_init(&L, d, ext, f1, f2);
     if (rc) return rc;
+    L.removed = removed;
     const int64_t V = L.V;
     unsigned char *inA = calloc((size_t)V, 1), *inB = calloc((size_t)V, 1);
     int64_t *label = calloc((size_t)V, sizeof(int64_t));
@@ -230,6 +236,12 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
     }
     rc = validate_sets(&L, A, nA, B, nB, inA, inB);
     if (rc) goto done;
+    if (removed)
+        for (int64_t v = 0; v < V; v++)
+            if (removed[v] && (inA[v] || inB[v])) {
+                rc = OR_INVALID;
+                goto done;
+            }
     for (int64_t v = 0; v < V; v++) {
         stamp[v] = -1;
         bq[v] = INT64_MIN;

@@ -72,6 +72,8 @@ def lib():
         L.csp_solve_async.argtypes = [vp, vp, i64, vp, i64, i64, ctypes.POINTER(CspOptions), vp, vp, i64]
         L.csp_get_labels.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
         L.csp_solve_static.argtypes = [ctypes.c_int, i64p, vp, vp, ctypes.c_int, vp, i64, vp, i64, i64, i64, vp, vp]
+        L.csp_reconstruct_path.argtypes = [vp, i64p, i64, i64p, i64, i64, ctypes.POINTER(CspResult), i64p, i64, i64p]
+        L.csp_reconstruct_path.restype = ctypes.c_int
         for f in ("csp_create_lattice", "csp_upload_weights", "csp_reserve", "csp_solve", "csp_solve_async",
                   "csp_get_labels", "csp_solve_static"):
             getattr(L, f).restype = ctypes.c_int
@@ -210,6 +212,20 @@ class Lattice:
                                      int(M), ctypes.byref(opt), _ptr(result_dev),
                                      _ptr(trace_dev) if trace_dev is not None else None,
                                      int(trace_cap)), "csp_solve_async")
+
+    def reconstruct(self, A, B, M: int, result: Optional[Result] = None, cap: int = 1 << 20) -> Optional[np.ndarray]:
+        """``csp_reconstruct_path``: the path (vertex ids, A end first), or None if infeasible."""
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
+        B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
+        res = None
+        if result is not None:
+            res = CspResult(*[int(getattr(result, name)) for name, _ in CspResult._fields_])
+        out = np.zeros(cap, np.int64)
+        n = ctypes.c_int64(0)
+        _check(lib().csp_reconstruct_path(self._h, A.ctypes.data_as(i64p), A.size, B.ctypes.data_as(i64p), B.size,
+                                          int(M), ctypes.byref(res) if res is not None else None,
+                                          out.ctypes.data_as(i64p), cap, ctypes.byref(n)), "csp_reconstruct_path")
+        return out[: n.value].copy() if n.value else None
 
     def labels(self) -> np.ndarray:
         out = np.zeros(self.V, np.int32)

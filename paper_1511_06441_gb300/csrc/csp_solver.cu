@@ -124,6 +124,23 @@ __global__ void k_mark_B(const int64_t *B, long long nB, uint32_t *isB, long lon
     }
 }
 
+// Vertices outside the graph G' of a reconstruction step (Section 1): their label and
+// offer are set to 2^31 - 1, which no water can beat, so no flow is ever launched into
+// them and they never launch one.  A removed vertex in B is an invalid request.
+__global__ void k_mark_removed(const int64_t *R, long long nR, const uint32_t *isB, long long V, int32_t *label,
+                               unsigned long long *offer, Control *ctl)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nR; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = R[i];
+        if (r < 0 || r >= V || ((isB[r >> 5] >> (r & 31)) & 1u)) {
+            atomicExch(&ctl->status_in, ST_INVALID);
+            continue;
+        }
+        label[r] = INT_MAX;
+        offer[r] = 0x7fffffffffffffffull;
+    }
+}
+
 // Initialization (Algorithm 3): Label(a) = M for a in A (the offer word mirrors it);
 // each distinct source is listed once (in the candidate list) for the seed launch.
 __global__ void k_mark_A(const int64_t *A, long long nA, const uint32_t *isB, long long V, int M, int32_t *label,
@@ -136,8 +153,8 @@ __global__ void k_mark_A(const int64_t *A, long long nA, const uint32_t *isB, lo
             atomicExch(&ctl->status_in, ST_INVALID);
             continue;
         }
-        if ((isB[a >> 5] >> (a & 31)) & 1u) {
-            atomicExch(&ctl->status_in, ST_INVALID);  // A and B must be disjoint
+        if (((isB[a >> 5] >> (a & 31)) & 1u) || label[a] == INT_MAX) {
+            atomicExch(&ctl->status_in, ST_INVALID);  // A and B must be disjoint; A must be in the graph
             continue;
         }
         label[a] = M;
@@ -258,7 +275,7 @@ int64_t default_pool_cap(const csp_lattice *L)
 // Enqueues one solve (set-up kernels + persistent kernel) on stream s.
 csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB, int64_t M,
                          const csp_options *opt, long long *trace_dev, int64_t trace_cap, int64_t *result_dev,
-                         cudaStream_t s)
+                         cudaStream_t s, const int64_t *R_dev = nullptr, int64_t nR = 0)
 {
     const int64_t V = L->V;
     CSP_CUDA(cudaMemsetAsync(L->label, 0, V * 4, s));
@@ -269,6 +286,9 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
     k_reset<<<1, 32, 0, s>>>(L->ctl);
     k_mark_B<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nB + 255) / 256)), 256, 0, s>>>(B_dev, nB, L->isB, V,
                                                                                                  L->ctl);
+    if (nR > 0)
+        k_mark_removed<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nR + 255) / 256)), 256, 0, s>>>(
+            R_dev, nR, L->isB, V, L->label, L->offer, L->ctl);
     k_mark_A<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nA + 255) / 256)), 256, 0, s>>>(
         A_dev, nA, L->isB, V, (int)M, L->label, L->offer, L->cand, L->ctl);
     CSP_CUDA(cudaGetLastError());
@@ -354,6 +374,10 @@ csp_status check_sets_host(const csp_lattice *L, const int64_t *A, int64_t nA, c
 }  // namespace
 
 // ---------------------------------------------------------------- C ABI
+
+static csp_status solve_host(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                             const csp_options *opt, csp_result *out, int64_t *trace, int64_t trace_cap,
+                             int64_t *trace_len, const int64_t *R, int64_t nR);
 
 extern "C" {
 
@@ -485,8 +509,20 @@ csp_status csp_solve_async(csp_lattice *L, const int64_t *A_dev, int64_t nA, con
 csp_status csp_solve(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
                      const csp_options *opt, csp_result *out, int64_t *trace, int64_t trace_cap, int64_t *trace_len)
 {
+    return solve_host(L, A, nA, B, nB, M, opt, out, trace, trace_cap, trace_len, nullptr, 0);
+}
+
+}  // extern "C"
+
+// One synchronous solve with host arrays; R (nullable, nR ids) lists vertices removed
+// from the graph (a reconstruction step).
+static csp_status solve_host(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                      const csp_options *opt, csp_result *out, int64_t *trace, int64_t trace_cap, int64_t *trace_len,
+                      const int64_t *R, int64_t nR)
+{
     if (!L || !out || M >= (1ll << 31) || M < -(1ll << 31) + 1) return CSP_ERR_INVALID;
     if (trace && trace_cap < 0) return CSP_ERR_INVALID;
+    if (nR < 0 || (nR > 0 && !R)) return CSP_ERR_INVALID;
     csp_status st = check_sets_host(L, A, nA, B, nB);
     if (st != CSP_OK) return st;
     cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
@@ -501,12 +537,13 @@ csp_status csp_solve(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t
         }
     }
     for (int attempt = 0;; attempt++) {
-        st = ensure_workspace(L, cap, nA + nB);
+        st = ensure_workspace(L, cap, nA + nB + nR);
         if (st != CSP_OK) return st;
         CSP_CUDA(cudaMemcpyAsync(L->sets, A, nA * 8, cudaMemcpyHostToDevice, s));
         CSP_CUDA(cudaMemcpyAsync(L->sets + nA, B, nB * 8, cudaMemcpyHostToDevice, s));
+        if (nR > 0) CSP_CUDA(cudaMemcpyAsync(L->sets + nA + nB, R, nR * 8, cudaMemcpyHostToDevice, s));
         st = enqueue_solve(L, L->sets, nA, L->sets + nA, nB, M, opt, trace ? L->trace : nullptr,
-                           trace ? L->trace_cap : 0, nullptr, s);
+                           trace ? L->trace_cap : 0, nullptr, s, nR > 0 ? L->sets + nA + nB : nullptr, nR);
         if (st != CSP_OK) return st;
         long long o[R_COUNT];
         CSP_CUDA(cudaMemcpyAsync(o, (char *)L->ctl + offsetof(Control, out), sizeof(o), cudaMemcpyDeviceToHost, s));
@@ -534,6 +571,65 @@ csp_status csp_solve(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t
         if (trace_len) *trace_len = trace ? o[R_TRACELEN] : 0;
         return (csp_status)o[R_STATUS];
     }
+}
+
+// Edge weight f2 of the edge leaving v in direction dir, from the device edge record.
+static csp_status edge_f2(csp_lattice *L, int64_t v, int dir, int64_t *w2)
+{
+    unsigned char rec[32];
+    CSP_CUDA(cudaMemcpy(rec, (const char *)L->rec + v * L->rec_bytes, L->rec_bytes, cudaMemcpyDeviceToHost));
+    if (L->wbytes == 1) *w2 = rec[2 * dir + 1];
+    else *w2 = ((const uint16_t *)rec)[2 * dir + 1];
+    return CSP_OK;
+}
+
+extern "C" {
+
+csp_status csp_reconstruct_path(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                                const csp_result *res, int64_t *path, int64_t cap, int64_t *len)
+{
+    if (!L || !A || !B || nA < 1 || nB < 1 || !len || (cap > 0 && !path)) return CSP_ERR_INVALID;
+    csp_result r{};
+    csp_status st;
+    if (res) {
+        r = *res;
+    } else {
+        st = csp_solve(L, A, nA, B, nB, M, nullptr, &r, nullptr, 0, nullptr);
+        if (st != CSP_OK) return st;
+    }
+    *len = 0;
+    if (r.F1 < 0) return CSP_OK;  // infeasible: no path
+    std::vector<int64_t> a(A, A + nA);
+    std::sort(a.begin(), a.end());
+    auto in_A = [&](int64_t v) { return std::binary_search(a.begin(), a.end(), v); };
+    // V' = V minus (B and the path found so far); B' = {Y}; M' = F2 - f2(x) + 1 (strict bound)
+    std::vector<int64_t> found{r.X};
+    std::vector<int64_t> removed(B, B + nB);
+    int64_t Y = r.x_src, dir = r.x_dir, F2 = r.F2;
+    while (!in_A(Y)) {
+        if ((int64_t)found.size() > L->V) return CSP_ERR_INVALID;  // cannot happen for a simple path
+        int64_t w2 = 0;
+        st = edge_f2(L, Y, (int)dir, &w2);
+        if (st != CSP_OK) return st;
+        removed.push_back(found.back());
+        csp_result q{};
+        st = solve_host(L, A, nA, &Y, 1, F2 - w2 + 1, nullptr, &q, nullptr, 0, nullptr, removed.data(),
+                        (int64_t)removed.size());
+        if (st != CSP_OK) return st;
+        if (q.F1 < 0 || q.X != Y) {
+            set_error("csp_reconstruct_path: a reconstruction step found no path");
+            return CSP_ERR_INVALID;
+        }
+        found.push_back(Y);
+        Y = q.x_src;
+        dir = q.x_dir;
+        F2 = q.F2;
+    }
+    found.push_back(Y);
+    *len = (int64_t)found.size();
+    if (*len > cap) return CSP_ERR_CAPACITY;
+    for (int64_t i = 0; i < *len; i++) path[i] = found[*len - 1 - i];
+    return CSP_OK;
 }
 
 csp_status csp_get_labels(csp_lattice *L, int32_t *labels_host)

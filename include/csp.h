@@ -242,6 +242,72 @@ csp_status csp_solve_batch(const csp_query *q, int64_t n, const csp_batch_option
 csp_status csp_reconstruct_path(csp_lattice *lat, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB,
                                 int64_t M, const csp_result *res, int64_t *path, int64_t cap, int64_t *len);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * A resident lattice answering a stream of queries with continuous batching: one
+ * persistent kernel stays on the GPU; its CTAs form fixed groups, each owning one query
+ * slot (its own labels, offers and flow pools).  A group claims the next submitted query
+ * as soon as it is free, so queries that arrive while others run overlap on the device.
+ * Queries travel through a ring in host-mapped memory; a query is admitted into the
+ * ring while an entry is free (memory-based admission: slots are allocated up front from
+ * the memory budget).  The paper solves one query at a time; this mode is an addition.
+ */
+typedef struct csp_server csp_server;
+
+typedef struct {
+    int32_t group_ctas;       /* CTAs per query slot; 0 = 8 */
+    int32_t max_groups;       /* query slots; 0 = as many as fit on the GPU */
+    int64_t pool_capacity;    /* flows per pool buffer per slot; 0 = max(2^16, V); a query that
+                                 overflows it reports CSP_ERR_CAPACITY */
+    int64_t memory_budget;    /* bytes for all slots together; 0 = no limit beyond max_groups */
+    int64_t queue_capacity;   /* ring entries (queries submitted and not yet collected); 0 = 4 x slots */
+    double session_seconds;   /* the persistent kernel gives up waiting after this long; 0 = 600 */
+} csp_server_options;
+
+/* One query: 1..64 sources; targets either an explicit list (B, 1..64 ids) or, with
+ * B = NULL, the hyperplane {v : c_{b_axis}(v) = b_coord}. */
+typedef struct {
+    const int64_t *A;
+    int64_t nA;
+    const int64_t *B;
+    int64_t nB;
+    int32_t b_axis;
+    int32_t reserved;
+    int64_t b_coord;
+    int64_t M;
+    int64_t max_cycles;       /* 0 = no limit */
+} csp_server_query;
+
+/* Allocates the slots and launches the persistent server kernel on its own stream.  The
+ * lattice must outlive the server; while the server runs it occupies the GPU. */
+csp_status csp_server_create(csp_lattice *lat, const csp_server_options *opt, csp_server **out);
+
+/* The server's slots (groups), CTAs per slot and ring size. */
+csp_status csp_server_info(const csp_server *s, int32_t *groups, int32_t *group_ctas, int64_t *queue_capacity);
+
+/* Submits a query without waiting; *ticket identifies it.  CSP_ERR_CAPACITY: no ring
+ * entry is free (collect results first).  CSP_ERR_INVALID: bad query. */
+csp_status csp_server_submit(csp_server *s, const csp_server_query *q, int64_t *ticket);
+
+/* Non-blocking: *done = 1 once the query's result is available (then copied to out and
+ * status, both nullable).  A result must be collected before queue_capacity further
+ * submissions reuse its ring entry (CSP_ERR_INVALID if it was overwritten). */
+csp_status csp_server_poll(csp_server *s, int64_t ticket, csp_result *out, int32_t *status, int32_t *done);
+
+/* Replays a stream: query i arrives arrival_s[i] seconds after the call starts (sorted),
+ * is submitted once a ring entry is free and collected when done.  latency_s[i] =
+ * completion - arrival; every output is nullable. */
+csp_status csp_server_replay(csp_server *s, const csp_server_query *q, const double *arrival_s, int64_t n,
+                             csp_result *out, int32_t *status, double *latency_s, double *makespan_s);
+
+/* Stops the server (after the queries already submitted) and frees it. */
+csp_status csp_server_destroy(csp_server *s);
+
+/* Baseline for serving benchmarks: the same stream answered one query at a time with
+ * csp_solve (one launch per query, in arrival order).  Same outputs as csp_server_replay. */
+csp_status csp_serve_plain_replay(csp_lattice *lat, const csp_server_query *q, const double *arrival_s, int64_t n,
+                                  csp_result *out, int32_t *status, double *latency_s, double *makespan_s);
+
 /* Copies the labels left by the last solve (V int32: M - F2 of the best water that has
  * reached each vertex by the final time, 0 if none) to labels_host. */
 csp_status csp_get_labels(csp_lattice *lat, int32_t *labels_host);

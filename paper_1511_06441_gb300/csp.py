@@ -393,3 +393,135 @@ def solve_batch(items, *, ctas: int = 0, max_group: int = 0, no_graph: bool = Fa
     stat = (ctypes.c_int32 * n)()
     _check(L.csp_solve_batch(q, n, ctypes.byref(opt), res, stat), "csp_solve_batch")
     return _results(res, n, stat)
+
+
+class CspServerOptions(ctypes.Structure):
+    _fields_ = [("group_ctas", ctypes.c_int32), ("max_groups", ctypes.c_int32), ("pool_capacity", i64),
+                ("memory_budget", i64), ("queue_capacity", i64), ("session_seconds", ctypes.c_double)]
+
+
+class CspServerQuery(ctypes.Structure):
+    _fields_ = [("A", i64p), ("nA", i64), ("B", i64p), ("nB", i64), ("b_axis", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("b_coord", i64), ("M", i64), ("max_cycles", i64)]
+
+
+def _server_api():
+    L = lib()
+    if not getattr(L, "_server_ready", False):
+        L.csp_server_create.argtypes = [vp, ctypes.POINTER(CspServerOptions), ctypes.POINTER(vp)]
+        L.csp_server_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), i64p]
+        L.csp_server_submit.argtypes = [vp, ctypes.POINTER(CspServerQuery), i64p]
+        L.csp_server_poll.argtypes = [vp, i64, ctypes.POINTER(CspResult), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.csp_server_replay.argtypes = [vp, ctypes.POINTER(CspServerQuery), dp, i64, ctypes.POINTER(CspResult),
+                                        ctypes.POINTER(ctypes.c_int32), dp, dp]
+        L.csp_server_destroy.argtypes = [vp]
+        L.csp_serve_plain_replay.argtypes = [vp, ctypes.POINTER(CspServerQuery), dp, i64, ctypes.POINTER(CspResult),
+                                             ctypes.POINTER(ctypes.c_int32), dp, dp]
+        for f in ("csp_server_create", "csp_server_info", "csp_server_submit", "csp_server_poll", "csp_server_replay",
+                  "csp_server_destroy", "csp_serve_plain_replay"):
+            getattr(L, f).restype = ctypes.c_int
+        L._server_ready = True
+    return L
+
+
+def _server_queries(queries, use_hyperplane=True):
+    """queries: objects with A, M and either (axis, coord) or an explicit B list."""
+    keep = []
+    arr = (CspServerQuery * len(queries))()
+    for i, q in enumerate(queries):
+        A = np.ascontiguousarray(np.asarray(q.A, dtype=np.int64).reshape(-1))
+        keep.append(A)
+        axis = getattr(q, "axis", -1)
+        if use_hyperplane and axis is not None and axis >= 0:
+            arr[i] = CspServerQuery(A.ctypes.data_as(i64p), A.size, None, 0, int(axis), 0, int(q.coord), int(q.M),
+                                    int(getattr(q, "max_cycles", 0)))
+        else:
+            B = np.ascontiguousarray(np.asarray(q.B, dtype=np.int64).reshape(-1))
+            keep.append(B)
+            arr[i] = CspServerQuery(A.ctypes.data_as(i64p), A.size, B.ctypes.data_as(i64p), B.size, -1, 0, 0,
+                                    int(q.M), int(getattr(q, "max_cycles", 0)))
+    return arr, keep
+
+
+def _replay_outputs(res, stat, lat_s, n):
+    out = _results(res, n, stat)
+    return out, np.array(lat_s[:n], dtype=np.float64)
+
+
+class Server:
+    """``csp_server_*``: a resident lattice answering a query stream with continuous batching."""
+
+    def __init__(self, lattice: "Lattice", *, group_ctas: int = 0, max_groups: int = 0, pool_capacity: int = 0,
+                 memory_budget: int = 0, queue_capacity: int = 0, session_seconds: float = 0.0):
+        L = _server_api()
+        opt = CspServerOptions(group_ctas, max_groups, pool_capacity, memory_budget, queue_capacity, session_seconds)
+        h = vp()
+        _check(L.csp_server_create(lattice.handle, ctypes.byref(opt), ctypes.byref(h)), "csp_server_create")
+        self._h = h
+        self._lattice = lattice
+        g, c, q = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+        _check(L.csp_server_info(h, ctypes.byref(g), ctypes.byref(c), ctypes.byref(q)), "csp_server_info")
+        self.groups, self.group_ctas, self.queue_capacity = g.value, c.value, q.value
+
+    def submit(self, query, use_hyperplane: bool = True) -> int:
+        arr, _keep = _server_queries([query], use_hyperplane)
+        t = ctypes.c_int64(-1)
+        _check(_server_api().csp_server_submit(self._h, arr, ctypes.byref(t)), "csp_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        res = CspResult()
+        st = ctypes.c_int32(0)
+        done = ctypes.c_int32(0)
+        _check(_server_api().csp_server_poll(self._h, ticket, ctypes.byref(res), ctypes.byref(st), ctypes.byref(done)),
+               "csp_server_poll")
+        if not done.value:
+            return None
+        r = Result(*[int(getattr(res, name)) for name, _ in CspResult._fields_])
+        r.status = st.value
+        return r
+
+    def replay(self, queries, arrival_s, use_hyperplane: bool = True):
+        """Returns (results, latencies in s, makespan in s)."""
+        n = len(queries)
+        arr, _keep = _server_queries(queries, use_hyperplane)
+        arrival = np.ascontiguousarray(np.asarray(arrival_s, dtype=np.float64))
+        res = (CspResult * n)()
+        stat = (ctypes.c_int32 * n)()
+        lat = np.zeros(n, np.float64)
+        mk = ctypes.c_double(0)
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(_server_api().csp_server_replay(self._h, arr, arrival.ctypes.data_as(dp), n, res, stat,
+                                               lat.ctypes.data_as(dp), ctypes.byref(mk)), "csp_server_replay")
+        out, lat = _replay_outputs(res, stat, lat, n)
+        return out, lat, mk.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            st = _server_api().csp_server_destroy(self._h)
+            self._h = None
+            _check(st, "csp_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plain_replay(lattice: "Lattice", queries, arrival_s):
+    """``csp_serve_plain_replay``: the same stream answered one query at a time by csp_solve."""
+    n = len(queries)
+    arr, _keep = _server_queries(queries, True)
+    arrival = np.ascontiguousarray(np.asarray(arrival_s, dtype=np.float64))
+    res = (CspResult * n)()
+    stat = (ctypes.c_int32 * n)()
+    lat = np.zeros(n, np.float64)
+    mk = ctypes.c_double(0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(_server_api().csp_serve_plain_replay(lattice.handle, arr, arrival.ctypes.data_as(dp), n, res, stat,
+                                                lat.ctypes.data_as(dp), ctypes.byref(mk)), "csp_serve_plain_replay")
+    out, lat = _replay_outputs(res, stat, lat, n)
+    return out, lat, mk.value

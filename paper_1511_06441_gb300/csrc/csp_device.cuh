@@ -742,11 +742,11 @@ __device__ __forceinline__ PassCounts read_counters(const Counters *c)
 // and fresh counters.  The group leader writes the result record.
 template <int D, typename W, bool TRACE>
 __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t (&parity)[2], uint32_t *s_warp,
-                          uint32_t *s_base, unsigned long long epoch0 = 0)
+                          uint32_t *s_base, unsigned long long &epoch)
 {
+    // epoch: barriers already passed on ctl->bar (updated)
     Control *ctl = P.ctl;
     const bool leader = g.leader();
-    unsigned long long epoch = epoch0;  // barriers already passed on ctl->bar
     const int M = P.M;
     const unsigned long long t_start = globaltimer_ns();
 
@@ -885,13 +885,26 @@ finish:
 
 // ---------------------------------------------------------------- set-up inside a kernel
 
+// Targets of a solve started inside a kernel: an explicit id list, or the hyperplane
+// {v : c_axis(v) = coord} (axis >= 0).
+struct TargetSet {
+    const int64_t *list64;
+    const uint32_t *list32;
+    long long n;
+    int axis;
+    long long coord;
+};
+
 // Initialization (Algorithm 3) by the CTAs of group g, for solves started inside a
 // persistent kernel: labels and offers cleared, B marked, Label(a) = M on A (the offer
 // word mirrors it) and the distinct sources listed in cand for the seed launch.  Invalid
 // ids or A and B overlapping set ctl->status_in.  Returns false if a barrier failed.
+// General form: sources as int64 (A64) or uint32 (A32) ids, targets as a TargetSet.
+// (A hyperplane needs the lattice's extents; they are recovered from the strides, so
+// stride[axis + 1] must be set for axis < d - 1 and 0 beyond the last dimension.)
 template <typename W>
-__device__ bool group_setup(const Params<W> &P, const Group &g, const int64_t *A, long long nA, const int64_t *B,
-                            long long nB, unsigned long long &epoch)
+__device__ bool group_setup_sets(const Params<W> &P, const Group &g, const int64_t *A64, const uint32_t *A32,
+                                 long long nA, const TargetSet &T, unsigned long long &epoch)
 {
     Control *ctl = P.ctl;
     const long long V = P.V;
@@ -911,15 +924,30 @@ __device__ bool group_setup(const Params<W> &P, const Group &g, const int64_t *A
         }
     }
     if (!group_sync(ctl, epoch, g, P.barrier_ns)) return false;
-    for (long long i = t0; i < nB; i += step) {
-        const long long b = B[i];
-        if (b < 0 || b >= V) atomicExch(&ctl->status_in, ST_INVALID);
-        else atomicOr(const_cast<uint32_t *>(P.isB) + (b >> 5), 1u << (b & 31));
+    if (T.axis >= 0) {
+        // hyperplane c_axis = coord: ids hi * (stride * n) + coord * stride + lo
+        const long long st = P.stride[T.axis];
+        const long long nk = T.axis + 1 < 4 && P.stride[T.axis + 1] ? P.stride[T.axis + 1] / st : V / st;
+        const long long count = V / nk;
+        if (T.coord < 0 || T.coord >= nk) {
+            if (g.leader()) atomicExch(&ctl->status_in, ST_INVALID);
+        } else {
+            for (long long i = t0; i < count; i += step) {
+                const long long b = (i / st) * st * nk + T.coord * st + (i % st);
+                atomicOr(const_cast<uint32_t *>(P.isB) + (b >> 5), 1u << (b & 31));
+            }
+        }
+    } else {
+        for (long long i = t0; i < T.n; i += step) {
+            const long long b = T.list64 ? T.list64[i] : (long long)T.list32[i];
+            if (b < 0 || b >= V) atomicExch(&ctl->status_in, ST_INVALID);
+            else atomicOr(const_cast<uint32_t *>(P.isB) + (b >> 5), 1u << (b & 31));
+        }
     }
     if (!group_sync(ctl, epoch, g, P.barrier_ns)) return false;
     const unsigned long long key = ((unsigned long long)(uint32_t)P.M << 32) | 0xffffffffull;
     for (long long i = t0; i < nA; i += step) {
-        const long long a = A[i];
+        const long long a = A64 ? A64[i] : (long long)A32[i];
         if (a < 0 || a >= V) {
             atomicExch(&ctl->status_in, ST_INVALID);
             continue;
@@ -936,6 +964,13 @@ __device__ bool group_setup(const Params<W> &P, const Group &g, const int64_t *A
         }
     }
     return group_sync(ctl, epoch, g, P.barrier_ns);
+}
+
+template <typename W>
+__device__ bool group_setup(const Params<W> &P, const Group &g, const int64_t *A, long long nA, const int64_t *B,
+                            long long nB, unsigned long long &epoch)
+{
+    return group_setup_sets<W>(P, g, A, nullptr, nA, TargetSet{B, nullptr, nB, -1, 0}, epoch);
 }
 
 }  // namespace csp

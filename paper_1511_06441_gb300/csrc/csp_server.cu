@@ -1,0 +1,508 @@
+// libcsp serving mode: one resident lattice, a stream of (A, B, M) queries, continuous
+// batching on the device.
+//
+// One persistent cooperative kernel runs for the whole session.  Its CTAs form fixed
+// groups; each group owns one query slot (labels, offers, arrival list, flow pools) and
+// loops: its leader claims the next query from a ring in host-mapped memory (written by
+// the host, which on Grace-Blackwell the GPU reads coherently), the group solves it with
+// the same cycle loop as csp_solve, and the leader publishes the result and a done flag
+// back to host memory.  Queries that arrive while others are running are picked up by
+// whichever group frees up first, so their work overlaps on the device; the host admits
+// a query into the ring only while the ring (one entry per slot plus a small backlog) has
+// room.  The paper solves one query at a time; this mode is an addition.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "csp.h"
+#include "csp_device.cuh"
+#include "csp_internal.h"
+
+using namespace csp;
+
+namespace {
+
+constexpr int kMaxInline = 64;  // sources (and explicit targets) carried in a descriptor
+
+struct QueryDesc {
+    long long ticket;  // ring position + 1 once written (0 = empty)
+    int nA, nB;        // nB = 0 with axis >= 0: hyperplane target
+    int axis, M;
+    long long coord;
+    long long max_cycles;
+    uint32_t A[kMaxInline];
+    uint32_t B[kMaxInline];
+};
+
+struct ResultSlot {
+    long long r[R_COUNT];
+    long long done;  // ticket of the query whose result this is (0 = none yet)
+    long long pad[15];
+};
+
+// Host-mapped control words (written by the host, read by the kernel and vice versa).
+struct HostCtl {
+    alignas(128) unsigned long long tail;  // queries written so far
+    alignas(128) int shutdown;             // 1 = no more queries: groups exit when idle
+    alignas(128) unsigned long long served;
+};
+
+struct GroupSlot {
+    int32_t *label;
+    unsigned long long *offer;
+    uint32_t *isB, *cand;
+    unsigned int cand_cap, pool_cap;
+    uint32_t *ed[2];
+    int32_t *qa[2];
+    int32_t *ta[2];
+    Control *ctl;
+    long long *result;  // device copy of the current query's result
+};
+
+struct ServerArgs {
+    const uint4 *rec;
+    long long V;
+    int stride[4];
+    const GroupSlot *slots;
+    int group_ctas;
+    unsigned long long *head;  // device: next ring position to claim
+    long long *mailbox;        // device: per group, the claimed position (or -1)
+    const HostCtl *hctl;       // host-mapped
+    const QueryDesc *ring;     // host-mapped
+    ResultSlot *results;       // host-mapped
+    long long ring_size;
+    unsigned long long session_ns;
+};
+
+template <int D, typename W>
+__global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs S)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ uint32_t s_warp[NWARP];
+    __shared__ uint32_t s_base[2];
+    init_stage_barriers(sm);
+    uint32_t parity[2] = {0u, 0u};
+    const int gid = blockIdx.x / S.group_ctas;
+    const Group g{(uint32_t)(blockIdx.x % S.group_ctas), (uint32_t)S.group_ctas};
+    const GroupSlot &slot = S.slots[gid];
+    Params<W> P{};
+    P.rec = S.rec;
+    P.V = S.V;
+    for (int k = 0; k < 4; k++) P.stride[k] = S.stride[k];
+    P.label = slot.label;
+    P.offer = slot.offer;
+    P.isB = slot.isB;
+    P.cand = slot.cand;
+    P.cand_cap = slot.cand_cap;
+    for (int b = 0; b < 2; b++) {
+        P.ed[b] = slot.ed[b];
+        P.qa[b] = slot.qa[b];
+        P.ta[b] = slot.ta[b];
+    }
+    P.pool_cap = slot.pool_cap;
+    P.ctl = slot.ctl;
+    P.result_dev = slot.result;
+    P.budget_ns = 120ull * 1000000000ull;
+    P.barrier_ns = S.session_ns;  // an idle group waits for work at its barrier
+    unsigned long long epoch = 0;
+    const unsigned long long t_begin = globaltimer_ns();
+    __shared__ long long s_pos;
+    __shared__ QueryDesc s_q;
+    for (;;) {
+        if (g.leader()) {
+            // claim the next written query (bounded by the session budget)
+            long long pos = -1;
+            for (unsigned int spin = 0;; ++spin) {
+                unsigned long long tail;
+                asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(tail) : "l"(&S.hctl->tail) : "memory");
+                const unsigned long long h = *(volatile unsigned long long *)S.head;
+                if (h < tail) {
+                    if (atomicCAS(S.head, h, h + 1) == h) {
+                        pos = (long long)h;
+                        break;
+                    }
+                    continue;
+                }
+                if (*(volatile const int *)&S.hctl->shutdown) break;
+                if ((spin & 255u) == 255u && globaltimer_ns() - t_begin > S.session_ns) break;
+                __nanosleep(spin < 64 ? 200 : 2000);
+            }
+            S.mailbox[gid] = pos;
+        }
+        if (!group_sync(P.ctl, epoch, g, P.barrier_ns)) break;
+        if (threadIdx.x == 0) s_pos = *(volatile long long *)&S.mailbox[gid];
+        __syncthreads();
+        const long long pos = s_pos;
+        if (pos < 0) break;
+        {
+            // the descriptor lives in host memory and ring entries are reused: read it with
+            // volatile (uncached) loads into shared memory
+            const volatile uint32_t *src = reinterpret_cast<const volatile uint32_t *>(&S.ring[pos % S.ring_size]);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&s_q);
+            for (int i = threadIdx.x; i < (int)(sizeof(QueryDesc) / 4); i += TPB) dst[i] = src[i];
+        }
+        __syncthreads();
+        const QueryDesc &q = s_q;
+        P.M = q.M;
+        P.max_cycles = q.max_cycles;
+        const TargetSet T{nullptr, q.nB > 0 ? q.B : nullptr, q.nB, q.nB > 0 ? -1 : q.axis, q.coord};
+        group_setup_sets<W>(P, g, nullptr, q.A, q.nA, T, epoch);
+        run_solve<D, W, false>(P, g, sm, parity, s_warp, s_base, epoch);
+        if (!group_sync(P.ctl, epoch, g, P.barrier_ns)) break;
+        if (g.leader()) {
+            ResultSlot &out = S.results[pos % S.ring_size];
+            for (int i = 0; i < R_COUNT; i++) out.r[i] = __ldcg(P.result_dev + i);
+            __threadfence_system();
+            asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&out.done), "l"(pos + 1) : "memory");
+        }
+    }
+}
+
+template <typename W>
+const void *server_kernel(int d)
+{
+    switch (d) {
+    case 1: return (const void *)&k_server<1, W>;
+    case 2: return (const void *)&k_server<2, W>;
+    case 3: return (const void *)&k_server<3, W>;
+    default: return (const void *)&k_server<4, W>;
+    }
+}
+
+constexpr size_t kSmem = sizeof(Smem);
+
+}  // namespace
+
+struct csp_server {
+    csp_lattice *lat = nullptr;
+    int groups = 0, group_ctas = 0;
+    long long ring_size = 0;
+    void *ws = nullptr;
+    GroupSlot *d_slots = nullptr;
+    unsigned long long *d_head = nullptr;
+    long long *d_mailbox = nullptr;
+    HostCtl *hctl = nullptr;  // pinned, mapped
+    QueryDesc *ring = nullptr;
+    ResultSlot *results = nullptr;
+    void *host_block = nullptr;
+    cudaStream_t stream = nullptr;
+    unsigned long long next = 0;  // tickets written so far
+    bool running = false;
+    double session_s = 600.0;
+};
+
+namespace {
+
+void fill_desc(QueryDesc &d, const csp_server_query &q, long long pos)
+{
+    std::memset(&d, 0, sizeof(d));
+    d.nA = (int)q.nA;
+    for (int i = 0; i < d.nA; i++) d.A[i] = (uint32_t)q.A[i];
+    d.nB = q.B ? (int)q.nB : 0;
+    for (int i = 0; i < d.nB; i++) d.B[i] = (uint32_t)q.B[i];
+    d.axis = q.B ? -1 : q.b_axis;
+    d.coord = q.b_coord;
+    d.M = (int)q.M;
+    d.max_cycles = q.max_cycles;
+    d.ticket = pos + 1;
+}
+
+bool valid_query(const csp_server *s, const csp_server_query &q)
+{
+    if (!q.A || q.nA < 1 || q.nA > kMaxInline || q.M >= (1ll << 31) || q.M < -(1ll << 31) + 1) return false;
+    if (q.B) {
+        if (q.nB < 1 || q.nB > kMaxInline) return false;
+    } else if (q.b_axis < 0 || q.b_axis >= s->lat->d || q.b_coord < 0 || q.b_coord >= s->lat->ext[q.b_axis]) {
+        return false;
+    }
+    return true;
+}
+
+void copy_result(const long long *o, csp_result *x, int32_t *status)
+{
+    x->F1 = o[R_F1];
+    x->X = o[R_X];
+    x->x_src = o[R_XSRC];
+    x->x_dir = o[R_XDIR];
+    x->F2 = o[R_F2];
+    x->cycles = o[R_CYCLES];
+    x->updates = o[R_UPDATES];
+    x->launched = o[R_LAUNCHED];
+    x->passes = o[R_PASSES];
+    x->max_pool = o[R_MAXPOOL];
+    x->arrivals = o[R_ARRIVALS];
+    x->improved = o[R_IMPROVED];
+    if (status) *status = (int32_t)o[R_STATUS];
+}
+
+}  // namespace
+
+extern "C" {
+
+csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_server **out)
+{
+    if (!L || !out) return CSP_ERR_INVALID;
+    *out = nullptr;
+    csp_server *s = new (std::nothrow) csp_server();
+    if (!s) return CSP_ERR_OOM;
+    s->lat = L;
+    const void *fn = L->wbytes == 1 ? server_kernel<uint8_t>(L->d) : server_kernel<uint16_t>(L->d);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TPB, kSmem);
+    if (e != cudaSuccess || per_sm < 1) {
+        delete s;
+        return e != cudaSuccess ? cuda_fail(e, "server kernel attributes") : CSP_ERR_CUDA;
+    }
+    const int max_ctas = per_sm * num_sms(L->device);
+    int gc = opt && opt->group_ctas > 0 ? opt->group_ctas : 8;
+    gc = std::max(1, std::min(gc, max_ctas));
+    int groups = max_ctas / gc;
+    if (opt && opt->max_groups > 0) groups = std::min(groups, opt->max_groups);
+    const int64_t V = L->V;
+    int64_t pool = opt && opt->pool_capacity > 0 ? opt->pool_capacity : std::max<int64_t>(1 << 16, V);
+    pool = std::min<int64_t>(pool, (int64_t)std::max(L->flow_bound, 1024ull));
+    const int64_t cand = std::max<int64_t>(V, std::min<int64_t>(2 * L->d * V, pool));
+    size_t per = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = per;
+        per = align_up(per + bytes, 256);
+        return o;
+    };
+    const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
+                 o_cand = take(cand * 4), o_ctl = take(sizeof(Control)), o_res = take(R_COUNT * 8);
+    size_t o_pool[2][3];
+    for (int b = 0; b < 2; b++)
+        for (int f = 0; f < 3; f++) o_pool[b][f] = take((pool + POOL_PAD) * 4);
+    if (opt && opt->memory_budget > 0) groups = (int)std::max<int64_t>(1, std::min<int64_t>(groups, opt->memory_budget / per));
+    s->groups = groups;
+    s->group_ctas = gc;
+    s->ring_size = opt && opt->queue_capacity > 0 ? opt->queue_capacity : 4 * groups;
+    e = cudaMalloc(&s->ws, per * groups);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_slots, groups * sizeof(GroupSlot));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_head, 256);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_mailbox, groups * sizeof(long long));
+    const size_t host_bytes = sizeof(HostCtl) + s->ring_size * (sizeof(QueryDesc) + sizeof(ResultSlot)) + 256;
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->host_block, host_bytes, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        csp_server_destroy(s);
+        return cuda_fail(e, "server allocation");
+    }
+    std::memset(s->host_block, 0, host_bytes);
+    s->hctl = (HostCtl *)s->host_block;
+    s->ring = (QueryDesc *)((char *)s->host_block + sizeof(HostCtl));
+    s->results = (ResultSlot *)((char *)s->ring + s->ring_size * sizeof(QueryDesc));
+    std::vector<GroupSlot> slots(groups);
+    char *ws = (char *)s->ws;
+    for (int i = 0; i < groups; i++) {
+        char *b = ws + per * i;
+        GroupSlot &g = slots[i];
+        g.label = (int32_t *)(b + o_label);
+        g.offer = (unsigned long long *)(b + o_offer);
+        g.isB = (uint32_t *)(b + o_isB);
+        g.cand = (uint32_t *)(b + o_cand);
+        g.cand_cap = (unsigned int)cand;
+        g.pool_cap = (unsigned int)pool;
+        for (int q = 0; q < 2; q++) {
+            g.ed[q] = (uint32_t *)(b + o_pool[q][0]);
+            g.qa[q] = (int32_t *)(b + o_pool[q][1]);
+            g.ta[q] = (int32_t *)(b + o_pool[q][2]);
+        }
+        g.ctl = (Control *)(b + o_ctl);
+        g.result = (long long *)(b + o_res);
+        e = cudaMemset(g.ctl, 0, sizeof(Control));
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_slots, slots.data(), groups * sizeof(GroupSlot), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(s->d_head, 0, 256);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    ServerArgs a{};
+    if (e == cudaSuccess) {
+        a.rec = (const uint4 *)L->rec;
+        a.V = V;
+        for (int k = 0; k < 4; k++) a.stride[k] = L->stride[k];
+        a.slots = s->d_slots;
+        a.group_ctas = gc;
+        a.head = s->d_head;
+        a.mailbox = s->d_mailbox;
+        void *p = nullptr;
+        e = cudaHostGetDevicePointer(&p, s->host_block, 0);
+        a.hctl = (const HostCtl *)p;
+        a.ring = (const QueryDesc *)((char *)p + sizeof(HostCtl));
+        a.results = (ResultSlot *)((char *)a.ring + s->ring_size * sizeof(QueryDesc));
+        a.ring_size = s->ring_size;
+        const double secs = opt && opt->session_seconds > 0 ? opt->session_seconds : 600.0;
+        a.session_ns = (unsigned long long)(secs * 1e9);
+        s->session_s = secs;
+    }
+    if (e == cudaSuccess) {
+        void *args[1] = {&a};
+        e = cudaLaunchCooperativeKernel(fn, dim3(groups * gc), dim3(TPB), args, kSmem, s->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        csp_server_destroy(s);
+        return cuda_fail(e, "server launch");
+    }
+    s->running = true;
+    *out = s;
+    return CSP_OK;
+}
+
+csp_status csp_server_info(const csp_server *s, int32_t *groups, int32_t *group_ctas, int64_t *queue_capacity)
+{
+    if (!s) return CSP_ERR_INVALID;
+    if (groups) *groups = s->groups;
+    if (group_ctas) *group_ctas = s->group_ctas;
+    if (queue_capacity) *queue_capacity = s->ring_size;
+    return CSP_OK;
+}
+
+csp_status csp_server_submit(csp_server *s, const csp_server_query *q, int64_t *ticket)
+{
+    if (!s || !q || !ticket || !s->running) return CSP_ERR_INVALID;
+    if (!valid_query(s, *q)) return CSP_ERR_INVALID;
+    const unsigned long long pos = s->next;
+    // the ring entry must be free: the query that last used it has been served
+    if (pos >= (unsigned long long)s->ring_size) {
+        const ResultSlot &old = s->results[pos % s->ring_size];
+        if (*(volatile long long *)&old.done != (long long)(pos - s->ring_size + 1)) return CSP_ERR_CAPACITY;
+    }
+    fill_desc(s->ring[pos % s->ring_size], *q, (long long)pos);
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *(volatile unsigned long long *)&s->hctl->tail = pos + 1;
+    s->next = pos + 1;
+    *ticket = (int64_t)pos;
+    return CSP_OK;
+}
+
+csp_status csp_server_poll(csp_server *s, int64_t ticket, csp_result *out, int32_t *status, int32_t *done)
+{
+    if (!s || !done || ticket < 0 || (unsigned long long)ticket >= s->next) return CSP_ERR_INVALID;
+    const ResultSlot &r = s->results[ticket % s->ring_size];
+    const long long d = *(volatile long long *)&r.done;
+    *done = d == ticket + 1;
+    if (d > ticket + 1) return CSP_ERR_INVALID;  // overwritten: the result was not collected in time
+    if (*done) {
+        std::atomic_thread_fence(std::memory_order_acquire);
+        long long o[R_COUNT];
+        std::memcpy(o, (const void *)r.r, sizeof(o));
+        if (out) copy_result(o, out, status);
+        else if (status) *status = (int32_t)o[R_STATUS];
+    }
+    return CSP_OK;
+}
+
+csp_status csp_server_replay(csp_server *s, const csp_server_query *q, const double *arrival_s, int64_t n,
+                             csp_result *out, int32_t *status, double *latency_s, double *makespan_s)
+{
+    if (!s || !q || !arrival_s || n < 0 || !s->running) return CSP_ERR_INVALID;
+    for (int64_t i = 0; i < n; i++)
+        if (!valid_query(s, q[i])) return CSP_ERR_INVALID;
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto now_s = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    std::vector<int64_t> ticket(n, -1);
+    std::vector<char> done(n, 0);
+    int64_t next = 0, finished = 0, first_open = 0;
+    while (finished < n) {
+        bool progress = false;
+        // admit arrived queries while a ring entry is free
+        while (next < n && arrival_s[next] <= now_s()) {
+            if (next >= s->ring_size && !done[next - s->ring_size]) break;  // its ring entry is still in use
+            int64_t t = -1;
+            const csp_status st = csp_server_submit(s, &q[next], &t);
+            if (st == CSP_ERR_CAPACITY) break;
+            if (st != CSP_OK) return st;
+            ticket[next++] = t;
+            progress = true;
+        }
+        // collect finished queries (in any order)
+        for (int64_t i = first_open; i < next; i++) {
+            if (done[i]) continue;
+            int32_t d = 0;
+            csp_result r{};
+            int32_t stt = 0;
+            const csp_status st = csp_server_poll(s, ticket[i], &r, &stt, &d);
+            if (st != CSP_OK) return st;
+            if (d) {
+                done[i] = 1;
+                finished++;
+                if (out) out[i] = r;
+                if (status) status[i] = stt;
+                if (latency_s) latency_s[i] = now_s() - arrival_s[i];
+                progress = true;
+            }
+        }
+        while (first_open < next && done[first_open]) first_open++;
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (now_s() > s->session_s + 60.0) return CSP_ERR_TIMEOUT;  // the kernel has given up by now
+    }
+    if (makespan_s) *makespan_s = now_s();
+    return CSP_OK;
+}
+
+csp_status csp_server_destroy(csp_server *s)
+{
+    if (!s) return CSP_ERR_INVALID;
+    csp_status st = CSP_OK;
+    if (s->running) {
+        *(volatile int *)&s->hctl->shutdown = 1;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        const cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "server shutdown");
+    }
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->host_block) cudaFreeHost(s->host_block);
+    if (s->d_mailbox) cudaFree(s->d_mailbox);
+    if (s->d_head) cudaFree(s->d_head);
+    if (s->d_slots) cudaFree(s->d_slots);
+    if (s->ws) cudaFree(s->ws);
+    delete s;
+    return st;
+}
+
+// Baseline for the serving benchmark: the same stream answered one query at a time by
+// csp_solve (one launch per query, the whole GPU each), in arrival order.
+csp_status csp_serve_plain_replay(csp_lattice *L, const csp_server_query *q, const double *arrival_s, int64_t n,
+                                  csp_result *out, int32_t *status, double *latency_s, double *makespan_s)
+{
+    if (!L || !q || !arrival_s || n < 0) return CSP_ERR_INVALID;
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto now_s = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    std::vector<int64_t> B;
+    for (int64_t i = 0; i < n; i++) {
+        while (now_s() < arrival_s[i]) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        const int64_t *Bp = q[i].B;
+        int64_t nB = q[i].nB;
+        if (!Bp) {  // expand the hyperplane into an id list
+            const int k = q[i].b_axis;
+            if (k < 0 || k >= L->d) return CSP_ERR_INVALID;
+            const int64_t st = L->stride[k], nk = L->ext[k], count = L->V / nk;
+            B.resize(count);
+            for (int64_t j = 0; j < count; j++) B[j] = (j / st) * st * nk + q[i].b_coord * st + (j % st);
+            Bp = B.data();
+            nB = count;
+        }
+        csp_options o{};
+        o.max_cycles = q[i].max_cycles;
+        csp_result r{};
+        const csp_status st = csp_solve(L, q[i].A, q[i].nA, Bp, nB, q[i].M, &o, &r, nullptr, 0, nullptr);
+        if (out) out[i] = r;
+        if (status) status[i] = st;
+        if (latency_s) latency_s[i] = now_s() - arrival_s[i];
+    }
+    if (makespan_s) *makespan_s = now_s();
+    return CSP_OK;
+}
+
+}  // extern "C"

@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_cycle(Params<W> P)
     __shared__ uint32_t s_base[2];
     init_stage_barriers(sm);
     uint32_t parity[2] = {0u, 0u};
-    run_solve<D, W, TRACE>(P, Group{blockIdx.x, gridDim.x}, sm, parity, s_warp, s_base);
+    unsigned long long epoch = 0;
+    run_solve<D, W, TRACE>(P, Group{blockIdx.x, gridDim.x}, sm, parity, s_warp, s_base, epoch);
 }
 
 // ---------------------------------------------------------------- host side

@@ -276,8 +276,10 @@ def serving_lattice(side: int = 48, d: int = 4, seed: int = 5):
 @dataclasses.dataclass
 class Query:
     A: np.ndarray
-    B: np.ndarray
+    B: np.ndarray          # the target hyperplane as an explicit id list
     M: int
+    axis: int = -1         # B = {v : c_axis(v) = coord}
+    coord: int = 0
 
 
 def serving_queries(n: int, extents: Sequence[int], seed: int = 5, start: int = 0) -> List[Query]:
@@ -306,8 +308,14 @@ def serving_queries(n: int, extents: Sequence[int], seed: int = 5, start: int = 
                 chosen.append(v)
                 if len(chosen) == nsrc:
                     break
-        out.append(Query(np.array(sorted(chosen), np.int64), B, M))
+        out.append(Query(np.array(sorted(chosen), np.int64), B, M, k, c))
     return out
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 5, stream: int = 77) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream of ``n`` requests at ``rate`` per second."""
+    u = uniform_unit(seed, stream, n)
+    return np.cumsum(-np.log1p(-u) / rate)
 
 
 def random_small_instance(seed: int, max_vertices: int = 16, dims=(1, 2, 3), f_lo=(0, 1),

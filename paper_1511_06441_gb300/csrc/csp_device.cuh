@@ -122,6 +122,8 @@ struct Params {
     long long max_cycles;
     unsigned long long budget_ns;   // wall-clock budget of one launch (watchdog)
     unsigned long long barrier_ns;  // longest wait at one barrier before giving up
+    uint32_t *touched;              // nullable: vertices whose label left 0 are appended here
+    unsigned int *touched_n;        // its length
 };
 
 // Dynamic shared memory of the cycle kernel: two input stages filled by bulk copies,
@@ -649,6 +651,7 @@ __device__ void launch(const Params<W> &P, const Group &g, int ob, uint32_t n_ca
             neighbour_labels<D>(P.offer, P.stride, V, v, Lw);
             if (lo32(ov) == code) {  // the winning arrival at v
                 Lv = (int)hi32(ov);
+                if (P.touched && __ldcg(P.label + v) == 0) P.touched[atomicAdd(P.touched_n, 1u)] = v;
                 P.label[v] = Lv;
                 st.improved++;
                 if (in_set(P.isB, v))
@@ -904,16 +907,20 @@ struct TargetSet {
 // stride[axis + 1] must be set for axis < d - 1 and 0 beyond the last dimension.)
 template <typename W>
 __device__ bool group_setup_sets(const Params<W> &P, const Group &g, const int64_t *A64, const uint32_t *A32,
-                                 long long nA, const TargetSet &T, unsigned long long &epoch)
+                                 long long nA, const TargetSet &T, unsigned long long &epoch, bool clear = true)
 {
+    // clear = false: labels, offers and the B bitmap are already zero (the previous
+    // solve on this workspace was undone by group_undo)
     Control *ctl = P.ctl;
     const long long V = P.V;
     const long long t0 = (long long)g.rank * TPB + threadIdx.x, step = (long long)g.size * TPB;
-    for (long long i = t0; i < V; i += step) {
-        P.label[i] = 0;
-        P.offer[i] = 0ull;
+    if (clear) {
+        for (long long i = t0; i < V; i += step) {
+            P.label[i] = 0;
+            P.offer[i] = 0ull;
+        }
+        for (long long i = t0; i < (V + 31) / 32; i += step) const_cast<uint32_t *>(P.isB)[i] = 0u;
     }
-    for (long long i = t0; i < (V + 31) / 32; i += step) const_cast<uint32_t *>(P.isB)[i] = 0u;
     if (g.leader()) {
         ctl->status_in = 0;
         for (int b = 0; b < 2; b++) {
@@ -971,6 +978,49 @@ __device__ bool group_setup(const Params<W> &P, const Group &g, const int64_t *A
                             long long nB, unsigned long long &epoch)
 {
     return group_setup_sets<W>(P, g, A, nullptr, nA, TargetSet{B, nullptr, nB, -1, 0}, epoch);
+}
+
+// Returns a workspace to all-zero labels, offers and B bitmap after a solve, touching
+// only what the solve changed: the vertices in P.touched (first improvements), the
+// sources and the targets.  Much cheaper than clearing V entries when a solve reaches a
+// small part of a large lattice.  Ends with a group barrier.
+template <typename W>
+__device__ bool group_undo(const Params<W> &P, const Group &g, const uint32_t *A32, long long nA, const TargetSet &T,
+                           unsigned long long &epoch)
+{
+    const long long t0 = (long long)g.rank * TPB + threadIdx.x, step = (long long)g.size * TPB;
+    const long long nt = (long long)*(volatile unsigned int *)P.touched_n;
+    for (long long i = t0; i < nt; i += step) {
+        const uint32_t v = __ldcg(P.touched + i);
+        P.label[v] = 0;
+        P.offer[v] = 0ull;
+    }
+    for (long long i = t0; i < nA; i += step) {
+        const uint32_t a = A32[i];
+        if (a < (uint32_t)P.V) {
+            P.label[a] = 0;
+            P.offer[a] = 0ull;
+        }
+    }
+    uint32_t *isB = const_cast<uint32_t *>(P.isB);
+    if (T.axis >= 0) {
+        const long long st = P.stride[T.axis];
+        const long long nk = T.axis + 1 < 4 && P.stride[T.axis + 1] ? P.stride[T.axis + 1] / st : P.V / st;
+        const long long count = P.V / nk;
+        if (T.coord >= 0 && T.coord < nk)
+            for (long long i = t0; i < count; i += step) {
+                const long long b = (i / st) * st * nk + T.coord * st + (i % st);
+                isB[b >> 5] = 0u;  // every bit set in this word belongs to the hyperplane
+            }
+    } else {
+        for (long long i = t0; i < T.n; i += step) {
+            const long long b = T.list64 ? T.list64[i] : (long long)T.list32[i];
+            if (b >= 0 && b < P.V) isB[b >> 5] = 0u;  // only target bits were set
+        }
+    }
+    if (!group_sync(P.ctl, epoch, g, P.barrier_ns)) return false;
+    if (g.leader()) *P.touched_n = 0u;
+    return group_sync(P.ctl, epoch, g, P.barrier_ns);
 }
 
 }  // namespace csp

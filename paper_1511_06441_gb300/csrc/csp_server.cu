@@ -63,6 +63,8 @@ struct GroupSlot {
     int32_t *ta[2];
     Control *ctl;
     long long *result;  // device copy of the current query's result
+    uint32_t *touched;  // vertices whose label left 0 during the current query
+    unsigned int *touched_n;
 };
 
 struct ServerArgs {
@@ -109,6 +111,8 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
     P.pool_cap = slot.pool_cap;
     P.ctl = slot.ctl;
     P.result_dev = slot.result;
+    P.touched = slot.touched;
+    P.touched_n = slot.touched_n;
     P.budget_ns = 120ull * 1000000000ull;
     P.barrier_ns = S.session_ns;  // an idle group waits for work at its barrier
     unsigned long long epoch = 0;
@@ -153,7 +157,9 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
         P.M = q.M;
         P.max_cycles = q.max_cycles;
         const TargetSet T{nullptr, q.nB > 0 ? q.B : nullptr, q.nB, q.nB > 0 ? -1 : q.axis, q.coord};
-        group_setup_sets<W>(P, g, nullptr, q.A, q.nA, T, epoch);
+        // the slot's labels, offers and B bitmap are all zero here (zeroed at creation and
+        // undone after every query), so the set-up touches only A and B
+        group_setup_sets<W>(P, g, nullptr, q.A, q.nA, T, epoch, false);
         run_solve<D, W, false>(P, g, sm, parity, s_warp, s_base, epoch);
         if (!group_sync(P.ctl, epoch, g, P.barrier_ns)) break;
         if (g.leader()) {
@@ -162,6 +168,7 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
             __threadfence_system();
             asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&out.done), "l"(pos + 1) : "memory");
         }
+        if (!group_undo<W>(P, g, q.A, q.nA, T, epoch)) break;
     }
 }
 
@@ -277,7 +284,8 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
         return o;
     };
     const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
-                 o_cand = take(cand * 4), o_ctl = take(sizeof(Control)), o_res = take(R_COUNT * 8);
+                 o_cand = take(cand * 4), o_ctl = take(sizeof(Control)), o_res = take(R_COUNT * 8),
+                 o_touched = take(V * 4), o_tn = take(256);
     size_t o_pool[2][3];
     for (int b = 0; b < 2; b++)
         for (int f = 0; f < 3; f++) o_pool[b][f] = take((pool + POOL_PAD) * 4);
@@ -318,9 +326,10 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
         }
         g.ctl = (Control *)(b + o_ctl);
         g.result = (long long *)(b + o_res);
-        e = cudaMemset(g.ctl, 0, sizeof(Control));
-        if (e != cudaSuccess) break;
+        g.touched = (uint32_t *)(b + o_touched);
+        g.touched_n = (unsigned int *)(b + o_tn);
     }
+    if (e == cudaSuccess) e = cudaMemset(ws, 0, per * groups);  // all labels, offers, bitmaps and controls
     if (e == cudaSuccess) e = cudaMemcpy(s->d_slots, slots.data(), groups * sizeof(GroupSlot), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(s->d_head, 0, 256);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);

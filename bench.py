@@ -245,7 +245,8 @@ def run_ours(args):
             with open(prof) as f:
                 pj = json.load(f)
             if pj.get("kernel_source_sha256") == _kernel_sha():
-                traffic = pj.get("traffic_bytes_per_launch")
+                per_m = pj.get("traffic_bytes_per_launch", {})
+                traffic = float(np.mean([per_m[str(M)] for M in M_SWEEP]))
         except Exception:
             traffic = None
 
@@ -293,7 +294,9 @@ def run_ours(args):
                        trace=bool(args.trace)),
         "results": {str(M): {"F1": int(r[1]), "X": int(r[2]), "x_src": int(r[3]), "x_dir": int(r[4]),
                              "F2": int(r[5]), "cycles": int(r[6]), "updates": int(r[7]), "passes": int(r[9]),
-                             "max_pool": int(r[10]), "kernel_ms": float(np.mean([kern_ms[k][i] for k in range(K)]))}
+                             "max_pool": int(r[10]), "arrivals": int(r[13]), "improved": int(r[14]),
+                             "launched": int(r[8]), "alg_bytes": alg_bytes[i],
+                             "kernel_ms": float(np.mean([kern_ms[k][i] for k in range(K)]))}
                     for i, (M, r) in enumerate(zip(M_SWEEP, out))},
         "instances_per_s": world * K * nM / total_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -301,13 +304,120 @@ def run_ours(args):
                      "kernel": "k_cycle (persistent cycle kernel)",
                      "algorithmic_bytes_per_launch": float(np.mean(alg_bytes)),
                      "kernel_ms_per_launch": kern_avg_ms},
-        "gpu_launches": 5 * nM * K,
+        "gpu_launches": 4 * nM * K,
         "clocks": clocks,
         "e2e": e2e,
     }
+    del lat, f1, f2, flush, trace, rec
+    torch.cuda.empty_cache()
+    if world == 1 and args.batch:
+        line["batched"] = bench_batched(csp, synth)
+    if world == 1 and args.serve > 0:
+        line["serving"] = bench_serving(csp, synth, args.serve)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, ORACLE_SAMPLE_CYCLES)
     print(json.dumps(line), flush=True)
+
+
+def bench_batched(csp, synth):
+    """512 mixed 2-D/3-D instances: one tuned batched launch vs one launch per instance."""
+    import torch
+    insts = synth.batch_instances(512)
+    lats = [csp.Lattice(i.extents, i.f1, i.f2) for i in insts]
+    items = [(L, i.A, i.B, i.M) for L, i in zip(lats, insts)]
+    b = csp.Batch(items)
+    s = torch.cuda.Stream()
+
+    def timed(run):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(s)
+        run()
+        ev[1].record(s)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1])
+
+    b.run(s)  # warm-up with the first-guess schedule, then one autotuner step on its measurements
+    torch.cuda.synchronize()
+    res0 = b.results()
+    b.tune(res0)
+    ms_b = timed(lambda: b.run(s))
+    res = b.results()
+    model = b.model()
+    sched = b.schedule()
+    devA = [torch.from_numpy(i.A).cuda() for i in insts]
+    devB = [torch.from_numpy(i.B).cuda() for i in insts]
+    rec = torch.zeros((len(insts), 16), dtype=torch.int64, device="cuda")
+    for L, i in zip(lats, insts):
+        L.reserve(max(1 << 16, 6 * i.V))
+    torch.cuda.synchronize()
+
+    def plain():
+        for k, (L, i) in enumerate(zip(lats, insts)):
+            L.solve_async(devA[k], devB[k], i.M, rec[k], stream=s)
+
+    ms_p = timed(plain)
+    r = rec.cpu().numpy()
+    agree = sum(1 for k in range(len(insts)) if r[k, 0] == 0 and tuple(int(x) for x in r[k, 1:6]) == res[k].answer())
+    upd = sum(x.updates for x in res)
+    b.close()
+    for L in lats:
+        L.close()
+    torch.cuda.empty_cache()
+    n = len(insts)
+    return {"workload": "batch512_mixed_2d32-1024_3d16-160_U1-32_faceA_faceB", "instances": n,
+            "instances_per_s": n / (ms_b / 1e3), "plain_instances_per_s": n / (ms_p / 1e3),
+            "speedup_vs_plain": ms_p / ms_b, "batched_ms": ms_b, "plain_ms": ms_p,
+            "updates_per_s": upd / (ms_b / 1e3), "updates": upd,
+            "statuses_ok": sum(1 for x in res if x.status == 0), "agree_with_plain": agree,
+            "schedule": {"ctas": sched["ctas"], "group_sizes": {str(g): int((sched["group"] == g).sum())
+                                                                for g in sorted(set(sched["group"].tolist()))},
+                         "planned_makespan_ms": model["makespan_us"] / 1e3,
+                         "model": {k: round(v, 3) for k, v in model.items() if k != "makespan_us"}},
+            "plain": "one cooperative launch per instance (csp_solve_async), sequential on one stream"}
+
+
+def bench_serving(csp, synth, n_queries):
+    """48^4 lattice, query stream served with continuous batching vs answered one at a time."""
+    import torch
+    ext, f1, f2 = synth.serving_lattice(48, 4, 5)
+    lat = csp.Lattice(ext, f1, f2)
+    qs = synth.serving_queries(n_queries, ext, seed=5)
+    t_svc = []
+    alone = []
+    for q in qs:
+        t0 = time.perf_counter()
+        alone.append(lat.solve(q.A, q.B, q.M))
+        t_svc.append(time.perf_counter() - t0)
+    mu = 1.0 / float(np.mean(t_svc))
+    key = lambda r: (r.answer(), r.cycles, r.updates)  # noqa: E731
+    max_pool = max(r.max_pool for r in alone)
+    rates = (0.25, 0.5, 0.75, 1.0, 1.25)
+    out = {"workload": f"lattice4d_48_U1-20_{n_queries}queries_1-64src_hyperplaneB_M200-2000",
+           "queries": n_queries, "plain_saturation_qps": mu, "service_ms_p50": 1e3 * float(np.median(t_svc)),
+           "rates": []}
+    srv = csp.Server(lat, group_ctas=32, pool_capacity=max(1 << 16, int(1.25 * max_pool)), session_seconds=600)
+    out["slots"] = srv.groups
+    out["ctas_per_slot"] = srv.group_ctas
+    served = {}
+    for m in rates:
+        arr = synth.poisson_arrivals(n_queries, m * mu, seed=5)
+        got, L, mk = srv.replay(qs, arr)
+        served[m] = (got, L, mk)
+    srv.close()
+    for m in rates:
+        got, L, mk = served[m]
+        arr = synth.poisson_arrivals(n_queries, m * mu, seed=5)
+        pg, PL, pmk = csp.plain_replay(lat, qs, arr)
+        out["rates"].append({
+            "rate_x_saturation": m, "rate_qps": m * mu,
+            "served": {"qps": n_queries / mk, "p50_ms": 1e3 * float(np.median(L)),
+                       "p99_ms": 1e3 * float(np.quantile(L, 0.99)),
+                       "equal_to_alone": sum(key(a) == key(b) for a, b in zip(got, alone))},
+            "plain": {"qps": n_queries / pmk, "p50_ms": 1e3 * float(np.median(PL)),
+                      "p99_ms": 1e3 * float(np.quantile(PL, 0.99))}})
+    lat.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def _kernel_sha():
@@ -329,6 +439,9 @@ def main():
     ap.add_argument("--trace", type=int, default=1, help="record the per-cycle trace (active set size) in the step")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=1, help="also measure 512 batched instances vs one launch each (N=1)")
+    ap.add_argument("--serve", type=int, default=2000,
+                    help="queries per rate for the serving comparison on the 48^4 lattice (0 = skip; N=1 only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

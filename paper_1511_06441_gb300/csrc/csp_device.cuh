@@ -455,8 +455,12 @@ __device__ __forceinline__ void write_flows(const Params<W> &P, int ob, Counters
 // processed the next one is already in flight.  With TRACE, live flows set their source's
 // bit in srcbits (counted by the launch phase).
 // Returns false if a copy wait timed out (ctl->err set).
+#ifndef CSP_PHASE_INLINE
+#define CSP_PHASE_INLINE __forceinline__
+#endif
+
 template <int D, typename W, bool TRACE>
-__device__ bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_in, int Tg, Counters *C, LocalStats &st,
+__device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_in, int Tg, Counters *C, LocalStats &st,
                       Smem &sm, uint32_t (&parity)[2], uint32_t *s_warp, uint32_t *s_base)
 {
     const int ob = ib ^ 1;
@@ -622,7 +626,7 @@ __device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters 
 // Its loads (offer[v], the edge record, the 2d neighbour labels) are issued together.
 // With TRACE, also counts (and clears) the source bitmap filled by the sweep.
 template <int D, typename W, bool TRACE>
-__device__ void launch(const Params<W> &P, const Group &g, int ob, uint32_t n_cand, int Time, Counters *C, LocalStats &st,
+__device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int ob, uint32_t n_cand, int Time, Counters *C, LocalStats &st,
                        Smem &sm, uint32_t *s_warp, uint32_t *s_base)
 {
     const uint32_t V = (uint32_t)P.V;
@@ -666,7 +670,7 @@ __device__ void launch(const Params<W> &P, const Group &g, int ob, uint32_t n_ca
 // Seed launch (Algorithm 3): water of quality M leaves every source a in A (listed in
 // cand as plain vertex ids, label M already set) along each edge with M - f2 > Label(w).
 template <int D, typename W>
-__device__ void seed(const Params<W> &P, const Group &g, uint32_t n_src, Counters *C, LocalStats &st, Smem &sm,
+__device__ CSP_PHASE_INLINE void seed(const Params<W> &P, const Group &g, uint32_t n_src, Counters *C, LocalStats &st, Smem &sm,
                      uint32_t *s_warp, uint32_t *s_base)
 {
     const uint32_t V = (uint32_t)P.V;
@@ -721,22 +725,44 @@ struct PassCounts {
     int min_ta;
 };
 
+// Thread 0 reads the pass counters with independent L2 loads (one round trip in all) and
+// shares them through shared memory; every CTA gets the same values after the pass's
+// barrier.  (Volatile loads by every thread would cost one serialised round trip per
+// field per warp.)
 __device__ __forceinline__ PassCounts read_counters(const Counters *c)
 {
-    PassCounts r;
-    const volatile Counters *vc = c;
-    const unsigned long long oc = vc->out_cand, li = vc->lau_imp;
-    r.n_out = lo32(oc);
-    r.n_cand = hi32(oc);
-    r.launched = lo32(li);
-    r.improved = hi32(li);
-    r.n_live = vc->live;
-    r.xkey = vc->xkey;
-    r.n_active = vc->n_active;
-    r.overflow = vc->overflow;
-    r.abort = vc->abort;
-    r.min_ta = vc->min_ta;
+    __shared__ PassCounts s_pc;
+    if (threadIdx.x == 0) {
+        const unsigned long long oc = __ldcg(&c->out_cand), li = __ldcg(&c->lau_imp);
+        const unsigned long long lv = __ldcg(&c->live), xk = __ldcg(&c->xkey);
+        const unsigned int act = __ldcg(&c->n_active), ovf = __ldcg(&c->overflow), ab = __ldcg(&c->abort);
+        const int mt = __ldcg(&c->min_ta);
+        s_pc.n_out = lo32(oc);
+        s_pc.n_cand = hi32(oc);
+        s_pc.launched = lo32(li);
+        s_pc.improved = hi32(li);
+        s_pc.n_live = lv;
+        s_pc.xkey = xk;
+        s_pc.n_active = act;
+        s_pc.overflow = ovf;
+        s_pc.abort = ab;
+        s_pc.min_ta = mt;
+    }
+    __syncthreads();
+    const PassCounts r = s_pc;
+    __syncthreads();  // s_pc may be rewritten by the next call
     return r;
+}
+
+// One counter word read by thread 0 and shared (see read_counters).
+__device__ __forceinline__ unsigned long long read_shared_u64(const unsigned long long *p)
+{
+    __shared__ unsigned long long s_v;
+    if (threadIdx.x == 0) s_v = __ldcg(p);
+    __syncthreads();
+    const unsigned long long v = s_v;
+    __syncthreads();
+    return v;
 }
 
 // Runs one whole solve (the cycle loop of Algorithm 1) on the CTAs of group g.  The
@@ -772,7 +798,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
     {
         // seed: water leaves A at Time 0 along every edge that can raise a label
         LocalStats st{0, 0, 0, 0, INT_MAX};
-        const uint32_t n_src = min(hi32(*(volatile unsigned long long *)&ctl->cnt[0].out_cand), P.cand_cap);
+        const uint32_t n_src = min(hi32(read_shared_u64(&ctl->cnt[0].out_cand)), P.cand_cap);
         seed<D, W>(P, g, n_src, &ctl->cnt[0], st, sm, s_warp, s_base);
         flush_stats(st, &ctl->cnt[0]);
         if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
@@ -786,11 +812,12 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
         }
         max_pool = c.n_out;
         int Tg = c.min_ta;
+        uint32_t n_pool = c.n_out;  // flows in the pool the next sweep reads
 
         for (long long pass = 1;; pass++) {
             const int ib = (int)((pass - 1) & 1), ob = ib ^ 1;
             Counters *C = &ctl->cnt[ob];
-            const uint32_t n_in = lo32(*(volatile unsigned long long *)&ctl->cnt[ib].out_cand);
+            const uint32_t n_in = n_pool;
             LocalStats sa{0, 0, 0, 0, INT_MAX};
             if (!sweep<D, W, TRACE>(P, g, ib, n_in, Tg, C, sa, sm, parity, s_warp, s_base)) {
                 status = ST_BARRIER;
@@ -801,7 +828,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             if (leader) zero_counters(&ctl->cnt[ib]);  // everyone has read n_in
             if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
             LocalStats sb{0, 0, 0, 0, INT_MAX};
-            const uint32_t n_cand = min(hi32(*(volatile unsigned long long *)&C->out_cand), P.cand_cap);
+            const uint32_t n_cand = min(hi32(read_shared_u64(&C->out_cand)), P.cand_cap);
             launch<D, W, TRACE>(P, g, ob, n_cand, Tg, C, sb, sm, s_warp, s_base);
             flush_stats(sb, C);
             if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
@@ -851,6 +878,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                 goto finish;
             }
             max_pool = max(max_pool, c.n_out);
+            n_pool = c.n_out;
             Tg = c.min_ta;
             if (P.max_cycles > 0 && cycle >= P.max_cycles) { status = ST_TIMEOUT; goto finish; }
             if (Tg >= TIME_LIMIT) { status = ST_CAPACITY; goto finish; }

@@ -63,10 +63,13 @@ typedef struct {
 
 typedef struct {
     int64_t max_cycles;     /* stop with CSP_ERR_TIMEOUT after this many cycles; 0 = no limit */
-    int64_t pool_capacity;  /* flows per pool buffer; 0 = automatic.  csp_solve doubles it and
-                               retries on overflow; csp_solve_async reports CSP_ERR_CAPACITY */
+    int64_t pool_capacity;  /* flow slots per pool buffer, rounded up to whole chunks of 2048; each
+                               CTA of a solve may leave up to two chunks part-filled in a pass.
+                               0 = automatic.  csp_solve doubles it and retries on overflow;
+                               csp_solve_async reports CSP_ERR_CAPACITY */
     int32_t ctas;           /* CTAs of the persistent kernel; 0 = chosen from the lattice size */
-    int32_t reserved;
+    int32_t time_limit_s;   /* watchdog of the cycle kernel in seconds; 0 = 120.  A solve that runs
+                               longer stops with CSP_ERR_TIMEOUT (the GPU is left usable) */
     void *stream;           /* cudaStream_t to run on; NULL = the legacy default stream */
     void *ev_begin;         /* nullable cudaEvent_t recorded on the stream just before the cycle kernel */
     void *ev_end;           /* nullable cudaEvent_t recorded just after it */
@@ -186,7 +189,9 @@ typedef struct {
     int32_t max_group;        /* largest CTA group for one instance (power of 2); 0 = 64 */
     int32_t no_graph;         /* 1 = launch directly instead of through a CUDA graph */
     int32_t reserved;
-    int64_t pool_capacity;    /* flows per pool buffer per instance; 0 = max(2^16, 6V) capped by the flow bound */
+    int64_t pool_capacity;    /* flow slots per pool buffer per instance (whole chunks of 2048, up to two
+                                 part-filled per CTA); 0 = max(2^16, 6V) capped by the flow bound, plus
+                                 two chunks per CTA of the largest group */
     int64_t max_cycles;       /* per instance; 0 = no limit */
 } csp_batch_options;
 
@@ -257,8 +262,10 @@ typedef struct csp_server csp_server;
 typedef struct {
     int32_t group_ctas;       /* CTAs per query slot; 0 = 8 */
     int32_t max_groups;       /* query slots; 0 = as many as fit on the GPU */
-    int64_t pool_capacity;    /* flows per pool buffer per slot; 0 = max(2^16, V); a query that
-                                 overflows it reports CSP_ERR_CAPACITY */
+    int64_t pool_capacity;    /* flow slots per pool buffer per slot (whole chunks of 2048, up to two
+                                 part-filled per CTA); 0 = max(2^16, V) capped by the flow bound, plus
+                                 two chunks per CTA of the slot; a query that overflows it reports
+                                 CSP_ERR_CAPACITY */
     int64_t memory_budget;    /* bytes for all slots together; 0 = no limit beyond max_groups */
     int64_t queue_capacity;   /* ring entries (queries submitted and not yet collected); 0 = 4 x slots */
     double session_seconds;   /* the persistent kernel gives up waiting after this long; 0 = 600 */

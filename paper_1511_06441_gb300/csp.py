@@ -38,7 +38,7 @@ class CspResult(ctypes.Structure):
 
 class CspOptions(ctypes.Structure):
     _fields_ = [("max_cycles", ctypes.c_int64), ("pool_capacity", ctypes.c_int64), ("ctas", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stream", vp), ("ev_begin", vp), ("ev_end", vp)]
+                ("time_limit_s", ctypes.c_int32), ("stream", vp), ("ev_begin", vp), ("ev_end", vp)]
 
 
 class CspError(RuntimeError):
@@ -127,9 +127,9 @@ def _event_handle(ev) -> Optional[int]:
 
 
 def options(max_cycles: int = 0, pool_capacity: int = 0, ctas: int = 0, stream=None,
-            ev_begin=None, ev_end=None) -> CspOptions:
-    return CspOptions(max_cycles, pool_capacity, ctas, 0, _stream_handle(stream), _event_handle(ev_begin),
-                      _event_handle(ev_end))
+            ev_begin=None, ev_end=None, time_limit_s: int = 0) -> CspOptions:
+    return CspOptions(max_cycles, pool_capacity, ctas, int(time_limit_s), _stream_handle(stream),
+                      _event_handle(ev_begin), _event_handle(ev_end))
 
 
 class Lattice:
@@ -181,11 +181,12 @@ class Lattice:
         _check(lib().csp_reserve(self._h, int(pool_capacity)), "csp_reserve")
 
     def solve(self, A, B, M: int, *, trace: bool = False, trace_cap: int = 1 << 16, max_cycles: int = 0,
-              pool_capacity: int = 0, ctas: int = 0, stream=None, check: bool = True) -> Result:
+              pool_capacity: int = 0, ctas: int = 0, stream=None, check: bool = True,
+              time_limit_s: int = 0) -> Result:
         """``csp_solve``: host sets in, host result out (blocks until done)."""
         A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
         B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
-        opt = options(max_cycles, pool_capacity, ctas, stream)
+        opt = options(max_cycles, pool_capacity, ctas, stream, time_limit_s=time_limit_s)
         res = CspResult()
         tr = np.zeros(3 * trace_cap, np.int64) if trace else None
         tl = ctypes.c_int64(0)
@@ -202,12 +203,13 @@ class Lattice:
         return out
 
     def solve_async(self, A_dev, B_dev, M: int, result_dev, *, trace_dev=None, trace_cap: int = 0,
-                    max_cycles: int = 0, ctas: int = 0, stream=None, ev_begin=None, ev_end=None):
+                    max_cycles: int = 0, ctas: int = 0, stream=None, ev_begin=None, ev_end=None,
+                    time_limit_s: int = 0):
         """``csp_solve_async``: device sets (int64 tensors), device result (16 int64).
 
         ``ev_begin``/``ev_end``: optional CUDA events recorded around the cycle kernel.
         """
-        opt = options(max_cycles, 0, ctas, stream, ev_begin, ev_end)
+        opt = options(max_cycles, 0, ctas, stream, ev_begin, ev_end, time_limit_s)
         _check(lib().csp_solve_async(self._h, _ptr(A_dev), int(A_dev.numel()), _ptr(B_dev), int(B_dev.numel()),
                                      int(M), ctypes.byref(opt), _ptr(result_dev),
                                      _ptr(trace_dev) if trace_dev is not None else None,

@@ -40,6 +40,7 @@ struct BatchInstance {
     uint32_t *ed[2];
     int32_t *qa[2];
     int32_t *ta[2];
+    uint32_t *fill[2];
     Control *ctl;
     long long *result;
     const int64_t *A, *B;
@@ -69,6 +70,7 @@ __device__ __forceinline__ Params<W> batch_params(const BatchInstance &I, unsign
         P.ed[b] = I.ed[b];
         P.qa[b] = I.qa[b];
         P.ta[b] = I.ta[b];
+        P.fill[b] = I.fill[b];
     }
     P.pool_cap = I.pool_cap;
     P.ctl = I.ctl;
@@ -88,10 +90,8 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-    __shared__ uint32_t s_warp[NWARP];
-    __shared__ uint32_t s_base[2];
     init_stage_barriers(sm);
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t parity[NSTAGE] = {};
     const int first = list_start[blockIdx.x], last = list_start[blockIdx.x + 1];
     for (int i = first; i < last; i++) {
         const BatchWork w = work[i];
@@ -101,10 +101,10 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM)
         unsigned long long epoch = 0;
         group_setup<W>(P, g, I.A, I.nA, I.B, I.nB, epoch);  // a failed barrier also fails the solve's first one
         switch (I.d) {
-        case 1: run_solve<1, W, false>(P, g, sm, parity, s_warp, s_base, epoch); break;
-        case 2: run_solve<2, W, false>(P, g, sm, parity, s_warp, s_base, epoch); break;
-        case 3: run_solve<3, W, false>(P, g, sm, parity, s_warp, s_base, epoch); break;
-        default: run_solve<4, W, false>(P, g, sm, parity, s_warp, s_base, epoch); break;
+        case 1: run_solve<1, W, false>(P, g, sm, parity, epoch); break;
+        case 2: run_solve<2, W, false>(P, g, sm, parity, epoch); break;
+        case 3: run_solve<3, W, false>(P, g, sm, parity, epoch); break;
+        default: run_solve<4, W, false>(P, g, sm, parity, epoch); break;
         }
         __syncthreads();
     }
@@ -366,23 +366,32 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
     b->inst.resize(n);
     b->stats.resize(n);
     struct Offs {
-        size_t label, offer, isB, cand, pool[2][3], A, B;
+        size_t label, offer, isB, cand, pool[2][3], fill[2], A, B;
     };
     std::vector<Offs> offs(n);
     for (int64_t i = 0; i < n; i++) {
         const csp_lattice *L = q[i].lat;
         const int64_t V = L->V;
-        int64_t pool = opt && opt->pool_capacity > 0 ? opt->pool_capacity : std::max<int64_t>(1 << 16, 6 * V);
-        pool = std::min<int64_t>(pool, (int64_t)std::max(L->flow_bound, 1024ull));
+        // default: 6V flows (at most the lattice's flow bound) plus the chunks a pass may leave
+        // part-filled; an explicit capacity is taken as given (rounded up to whole chunks)
+        int64_t pool = opt && opt->pool_capacity > 0
+                           ? opt->pool_capacity
+                           : std::min<int64_t>(std::max<int64_t>(1 << 16, 6 * V),
+                                               (int64_t)std::max(L->flow_bound, 1024ull)) +
+                                 chunk_slack(std::min(b->max_group, b->ctas));
         pool = std::min<int64_t>(pool, 0xF0000000ll);
-        const int64_t cand = std::max<int64_t>(V, std::min<int64_t>(2 * L->d * V, pool));
+        pool = (pool + TILE - 1) / TILE * TILE;  // whole chunks
+        // one candidate region per CTA of the instance's group (at most max_group CTAs)
+        const int64_t cand = std::max<int64_t>(V, pool + (int64_t)std::min(b->max_group, b->ctas) * TILE);
         Offs &o = offs[i];
         o.label = take(V * 4);
         o.offer = take(V * 8);
         o.isB = take(((V + 31) / 32) * 4);
         o.cand = take(cand * 4);
-        for (int bb = 0; bb < 2; bb++)
+        for (int bb = 0; bb < 2; bb++) {
             for (int f = 0; f < 3; f++) o.pool[bb][f] = take((pool + POOL_PAD) * 4);
+            o.fill[bb] = take((pool / TILE + 1) * 4);
+        }
         o.A = take(q[i].nA * 8);
         o.B = take(q[i].nB * 8);
         BatchInstance &I = b->inst[i];
@@ -425,6 +434,7 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
             I.ed[bb] = (uint32_t *)(ws + o.pool[bb][0]);
             I.qa[bb] = (int32_t *)(ws + o.pool[bb][1]);
             I.ta[bb] = (int32_t *)(ws + o.pool[bb][2]);
+            I.fill[bb] = (uint32_t *)(ws + o.fill[bb]);
         }
         I.A = (const int64_t *)(ws + o.A);
         I.B = (const int64_t *)(ws + o.B);

@@ -9,9 +9,11 @@
 //                     its high half equals label[] at every cycle boundary
 //   isB[V/32] uint32  bitmap of B
 //   srcbits   uint32  bitmap of the sources of live flows (trace mode), cleared each pass
-//   cand[]    uint32  arrivals of the current cycle (flow word ed of each arriving flow)
+//   cand[]    uint32  arrivals of the current cycle (flow word ed of each arriving flow),
+//                     one region of cand_cap / G entries per CTA of the group
 //   pool[2]   SoA     ed = dst << 3 | direction back to the source (uint32),
-//                     qa = quality on arrival (int32), ta = arrival time (int32)
+//                     qa = quality on arrival (int32), ta = arrival time (int32);
+//                     stored in chunks of TILE slots, fill[b][chunk] = slots in use
 // A flow is the paper's water flow on an active (or phantom) edge: it left its source
 // at the time the source's label last improved and carries that label.
 #pragma once
@@ -36,6 +38,7 @@ constexpr int TILE = TPB * IPT;     // items per tile
 constexpr int NWARP = TPB / 32;
 constexpr int TIME_LIMIT = 1 << 30; // arrival times must stay below this
 constexpr int POOL_PAD = 64;        // extra elements after each pool array (bulk copies round up)
+constexpr int NSTAGE = 3;           // input stages of the sweep (tiles in flight per CTA)
 
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_OOM = 2, ST_CUDA = 3, ST_CAPACITY = 4, ST_TIMEOUT = 5, ST_BARRIER = 6 };
 
@@ -60,6 +63,7 @@ struct Counters {
     alignas(128) unsigned int n_active;        // distinct sources of live flows (trace mode)
     alignas(128) unsigned int overflow;        // an output list ran out of room
     unsigned int abort;                        // set by the leader when the solve exceeded its time budget
+    alignas(128) unsigned int chunks;          // output-pool chunks handed out in this pass
 };
 
 constexpr int NRELEASE = 32;  // copies of the barrier's release word, one per 128-byte line
@@ -113,7 +117,8 @@ struct Params {
     uint32_t *ed[2];
     int32_t *qa[2];
     int32_t *ta[2];
-    unsigned int pool_cap;
+    uint32_t *fill[2];             // slots in use per pool chunk (pool_cap / TILE entries)
+    unsigned int pool_cap;         // slots per pool buffer, a multiple of TILE
     Control *ctl;
     long long *trace;              // device rows (Time, active, flows), nullable
     long long trace_cap;
@@ -126,17 +131,25 @@ struct Params {
     unsigned int *touched_n;        // its length
 };
 
-// Dynamic shared memory of the cycle kernel: two input stages filled by bulk copies,
-// one output staging tile, and the two stage barriers.
+// Dynamic shared memory of the cycle kernel: NSTAGE input stages filled by bulk copies,
+// their barriers, and the CTA's output cursor.  The cursor word packs the chunk being
+// filled (high half) and the slots already claimed in it (low half); next_chunk is the
+// chunk allocated ahead for the warp that fills the current one.
 struct Smem {
-    uint32_t in_ed[2][TILE];
-    int32_t in_qa[2][TILE];
-    int32_t in_ta[2][TILE];
-    uint32_t out_ed[TILE];
-    int32_t out_qa[TILE];
-    int32_t out_ta[TILE];
-    unsigned long long mbar[2];
+    uint32_t in_ed[NSTAGE][TILE];
+    int32_t in_qa[NSTAGE][TILE];
+    int32_t in_ta[NSTAGE][TILE];
+    unsigned long long mbar[NSTAGE];
+    unsigned long long cursor;
+    uint32_t next_chunk;
+    uint32_t n_cand;               // arrivals listed in this CTA's candidate region
+    uint32_t read_cnt[NSTAGE];     // warps done reading stage s
+    uint32_t stage_fill[NSTAGE];   // flows in the tile held by stage s
+    int fail;                      // a bounded wait gave up
 };
+
+constexpr uint32_t NO_CHUNK = 0xffffffffu;   // no chunk allocated
+constexpr uint32_t OVF_CHUNK = 0xfffffffeu;  // allocation beyond the pool: writes dropped, overflow set
 
 // The CTAs that cooperate on one solve: the whole grid for a single solve, a slice of
 // it in batched mode.  rank = index of this CTA in the group.
@@ -171,32 +184,6 @@ __device__ __forceinline__ uint32_t arrival_code(const int (&stride)[4], uint32_
     const uint32_t dst = ed >> 3, r = ed & 7u;
     const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(stride, r));
     return 0xffffffffu - (src * 8u + (r ^ 1u));
-}
-
-// Exclusive block-wide prefix sum of x; *total receives the block sum.
-__device__ __forceinline__ uint32_t block_scan_excl(uint32_t x, uint32_t &total, uint32_t *s_warp)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t v = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) s_warp[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < NWARP ? s_warp[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < NWARP) s_warp[lane] = w;
-    }
-    __syncthreads();
-    total = s_warp[NWARP - 1];
-    return (warp ? s_warp[warp - 1] : 0u) + v - x;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns()
@@ -312,59 +299,65 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Thread 0: starts the bulk copy of pool tile `tile` (buffer ib) into input stage s.
+// One lane: starts the bulk copy of pool chunk `tile` (buffer ib) into input stage s.
+// A chunk holds fill[ib][tile] flows; the copy is rounded up to 16 bytes and the slots
+// past the fill are ignored.  An empty chunk completes the stage without a copy.
 template <typename W>
-__device__ __forceinline__ void issue_tile(const Params<W> &P, Smem &sm, int s, int ib, uint32_t tile, uint32_t n_in)
+__device__ __forceinline__ void issue_tile(const Params<W> &P, Smem &sm, int s, int ib, uint32_t tile)
 {
+    const uint32_t n = min((uint32_t)TILE, __ldcg(P.fill[ib] + tile));
     const uint32_t start = tile * (uint32_t)TILE;
-    const uint32_t n = min((uint32_t)TILE, n_in - start);
-    const uint32_t bytes = ((n + 3u) & ~3u) * 4u;  // round up to 16 bytes (pool arrays are padded)
+    const uint32_t bytes = ((n + 3u) & ~3u) * 4u;
+    sm.stage_fill[s] = n;
     mbar_expect_tx(&sm.mbar[s], 3u * bytes);
-    bulk_g2s(sm.in_ed[s], P.ed[ib] + start, bytes, &sm.mbar[s]);
-    bulk_g2s(sm.in_qa[s], P.qa[ib] + start, bytes, &sm.mbar[s]);
-    bulk_g2s(sm.in_ta[s], P.ta[ib] + start, bytes, &sm.mbar[s]);
+    if (bytes) {
+        bulk_g2s(sm.in_ed[s], P.ed[ib] + start, bytes, &sm.mbar[s]);
+        bulk_g2s(sm.in_qa[s], P.qa[ib] + start, bytes, &sm.mbar[s]);
+        bulk_g2s(sm.in_ta[s], P.ta[ib] + start, bytes, &sm.mbar[s]);
+    }
 }
 
-// All threads wait for stage s (bounded).  Returns false, uniformly across the CTA, if
-// the copy did not complete in time (ctl->err is then set).
-__device__ __forceinline__ bool wait_stage(Smem &sm, int s, uint32_t parity, Control *ctl)
+// The calling warp waits for stage s (bounded).  Returns false if the copy did not
+// complete in time.
+__device__ __forceinline__ bool wait_stage_warp(Smem &sm, int s, uint32_t parity)
 {
-    bool ok = false;
     for (uint32_t i = 0; i < (1u << 22); i++)
-        if (mbar_try_wait(&sm.mbar[s], parity)) {
-            ok = true;
-            break;
-        }
-    const int bad = __syncthreads_or(!ok);
-    if (bad) {
-        if (threadIdx.x == 0) atomicExch(&ctl->err, 1);
-        // give a late copy a last chance to land before the CTA leaves
-        for (uint32_t i = 0; i < (1u << 20) && !mbar_try_wait(&sm.mbar[s], parity); i++) {
-        }
-        return false;
-    }
-    return true;
+        if (mbar_try_wait(&sm.mbar[s], parity)) return true;
+    return false;
+}
+
+// After a failed wait: gives copies still in flight into any stage a last chance to land
+// before the CTA leaves (thread 0; bounded).
+__device__ __forceinline__ void drain_stages(Smem &sm, const uint32_t (&parity)[NSTAGE], const bool (&pending)[NSTAGE])
+{
+    if (threadIdx.x == 0)
+        for (int s = 0; s < NSTAGE; s++)
+            if (pending[s])
+                for (uint32_t i = 0; i < (1u << 20) && !mbar_try_wait(&sm.mbar[s], parity[s]); i++) {
+                }
 }
 
 struct LocalStats {
-    uint32_t live, launched, improved, active;
+    uint32_t live, launched, improved, active, written, cands;
     int min_ta;
 };
 
 // Adds this block's statistics to the pass counters (one global atomic per word per CTA).
 __device__ __forceinline__ void flush_stats(const LocalStats &st, Counters *C)
 {
-    __shared__ unsigned long long s_live, s_li;
+    __shared__ unsigned long long s_live, s_li, s_oc;
     __shared__ unsigned int s_act;
     __shared__ int s_min;
     if (threadIdx.x == 0) {
         s_live = 0;
         s_li = 0;
+        s_oc = 0;
         s_act = 0;
         s_min = INT_MAX;
     }
     __syncthreads();
-    uint32_t live = st.live, lau = st.launched, imp = st.improved, act = st.active;
+    uint32_t live = st.live, lau = st.launched, imp = st.improved, act = st.active, wr = st.written,
+             cd = st.cands;
     int mn = st.min_ta;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -372,11 +365,14 @@ __device__ __forceinline__ void flush_stats(const LocalStats &st, Counters *C)
         lau += __shfl_xor_sync(0xffffffffu, lau, o);
         imp += __shfl_xor_sync(0xffffffffu, imp, o);
         act += __shfl_xor_sync(0xffffffffu, act, o);
+        wr += __shfl_xor_sync(0xffffffffu, wr, o);
+        cd += __shfl_xor_sync(0xffffffffu, cd, o);
         mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (live) atomicAdd(&s_live, (unsigned long long)live);
         if (lau | imp) atomicAdd(&s_li, (unsigned long long)lau | ((unsigned long long)imp << 32));
+        if (wr | cd) atomicAdd(&s_oc, (unsigned long long)wr | ((unsigned long long)cd << 32));
         if (act) atomicAdd(&s_act, act);
         if (mn != INT_MAX) atomicMin(&s_min, mn);
     }
@@ -384,63 +380,140 @@ __device__ __forceinline__ void flush_stats(const LocalStats &st, Counters *C)
     if (threadIdx.x == 0) {
         if (s_live) atomicAdd(&C->live, s_live);
         if (s_li) atomicAdd(&C->lau_imp, s_li);
+        if (s_oc) atomicAdd(&C->out_cand, s_oc);
         if (s_act) atomicAdd(&C->n_active, s_act);
         if (s_min != INT_MAX) atomicMin(&C->min_ta, s_min);
     }
 }
 
-// Reserves room for this tile's output with ONE 64-bit atomic on (flows | arrivals << 32):
-// a block-wide scan of the packed per-thread counts gives each thread its offsets.
-// s_base[0..1] receive the tile's global bases (valid after the next __syncthreads).
-__device__ __forceinline__ void reserve_tile(uint32_t nk, uint32_t nt, Counters *C, uint32_t &pk, uint32_t &pt,
-                                             uint32_t &tk, uint32_t &tt, uint32_t *s_warp, uint32_t *s_base)
+// ---------------------------------------------------------------- output cursor
+
+__device__ __forceinline__ unsigned long long pack_cursor(uint32_t chunk, uint32_t fill)
 {
-    uint32_t total;
-    const uint32_t pre = block_scan_excl(nk | (nt << 16), total, s_warp);
-    pk = pre & 0xffffu;
-    pt = pre >> 16;
-    tk = total & 0xffffu;
-    tt = total >> 16;
+    return ((unsigned long long)chunk << 32) | fill;
+}
+
+// Thread 0, at the start of a pass of a CTA that will write flows: allocates the chunk to
+// fill and the one after it with one atomic.  (A CTA with nothing to write allocates
+// nothing; its cursor holds NO_CHUNK.)
+__device__ __forceinline__ void cursor_open(Smem &sm, Counters *C, uint32_t n_chunks, bool will_write)
+{
+    uint32_t c0 = NO_CHUNK, c1 = NO_CHUNK;
+    if (will_write) {
+        const uint32_t c = atomicAdd(&C->chunks, 2u);
+        c0 = c < n_chunks ? c : OVF_CHUNK;
+        c1 = c + 1 < n_chunks ? c + 1 : OVF_CHUNK;
+    }
+    sm.cursor = pack_cursor(c0, 0);
+    sm.next_chunk = c1;
+}
+
+// Slots [f0, f0 + n) of the CTA's output, the part from TILE on in chunk c1.
+struct Span {
+    uint32_t c0, f0, c1;
+};
+
+// Warp-collective (all lanes, n >= 1 the same in every lane): claims n consecutive output
+// slots from the CTA's cursor with one shared-memory atomic.  The warp whose slots reach
+// the end of the current chunk moves the cursor to the chunk allocated ahead and
+// allocates the next one (a global atomic, off the other warps' path); a warp whose
+// atomic landed past the end waits for that move and retries.  The filled chunk's entry
+// of fill_out (the output buffer's fill array) becomes TILE.  Every wait is bounded: on
+// give-up the span's chunks are OVF_CHUNK (writes dropped), sm.fail and ctl->err are set.
+__device__ __forceinline__ Span claim_slots(Smem &sm, Counters *C, Control *ctl, uint32_t *fill_out, uint32_t n,
+                                            uint32_t n_chunks)
+{
+    uint32_t c0 = OVF_CHUNK, f0 = 0, c1 = OVF_CHUNK;
+    if ((threadIdx.x & 31) == 0) {
+        volatile unsigned long long *vcur = &sm.cursor;
+        volatile uint32_t *vnext = &sm.next_chunk;
+        bool done = false;
+        for (uint32_t tries = 0; tries < 4096u && !done; tries++) {
+            const unsigned long long old = atomicAdd(&sm.cursor, (unsigned long long)n);
+            const uint32_t id = hi32(old), f = lo32(old);
+            if (f + n < (uint32_t)TILE) {  // inside the current chunk
+                c0 = id;
+                f0 = f;
+                done = true;
+            } else if (f < (uint32_t)TILE) {  // this warp fills the chunk: move the cursor on
+                uint32_t nx = NO_CHUNK;
+                for (uint32_t spin = 0; spin < (1u << 22); spin++) {
+                    const uint32_t v = *vnext;
+                    if (v == OVF_CHUNK || (v != NO_CHUNK && v != id)) {  // (a stale value equals id)
+                        nx = v;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                if (nx == NO_CHUNK) break;  // gave up
+                *vnext = NO_CHUNK;
+                __threadfence_block();
+                atomicExch(&sm.cursor, pack_cursor(nx, f + n - (uint32_t)TILE));
+                if (id < OVF_CHUNK) fill_out[id] = (uint32_t)TILE;
+                c0 = id;
+                f0 = f;
+                c1 = nx;
+                done = true;
+                const uint32_t c = nx == OVF_CHUNK ? n_chunks : atomicAdd(&C->chunks, 1u);
+                *vnext = c < n_chunks ? c : OVF_CHUNK;
+            } else {
+                // landed past the end: wait until the filling warp has moved the cursor
+                uint32_t spin = 0;
+                for (; spin < (1u << 22) && hi32(*vcur) == id; spin++) __nanosleep(32);
+                if (spin >= (1u << 22)) break;
+            }
+        }
+        if (!done) {
+            c0 = c1 = OVF_CHUNK;
+            f0 = 0;
+            sm.fail = 1;
+            atomicExch(&ctl->err, 1);
+        }
+    }
+    Span sp;
+    sp.c0 = __shfl_sync(0xffffffffu, c0, 0);
+    sp.f0 = __shfl_sync(0xffffffffu, f0, 0);
+    sp.c1 = __shfl_sync(0xffffffffu, c1, 0);
+    return sp;
+}
+
+// Global slot of position p of a span (NO index if its chunk overflowed).
+__device__ __forceinline__ bool span_slot(const Span &sp, uint32_t p, uint32_t &idx)
+{
+    const uint32_t c = p < (uint32_t)TILE ? sp.c0 : sp.c1;
+    idx = c * (uint32_t)TILE + (p < (uint32_t)TILE ? p : p - (uint32_t)TILE);
+    return c < OVF_CHUNK;
+}
+
+// Thread 0, after the pass's last write (a __syncthreads in between): records how full the
+// CTA's last chunk is and marks the chunk allocated ahead as empty.
+template <typename W>
+__device__ __forceinline__ void cursor_close(const Params<W> &P, Smem &sm, int ob)
+{
     if (threadIdx.x == 0) {
-        unsigned long long old = 0;
-        if (tk | tt) old = atomicAdd(&C->out_cand, (unsigned long long)tk | ((unsigned long long)tt << 32));
-        s_base[0] = lo32(old);
-        s_base[1] = hi32(old);
+        const unsigned long long cur = sm.cursor;
+        const uint32_t id = hi32(cur), nx = sm.next_chunk;
+        if (id < OVF_CHUNK) P.fill[ob][id] = min(lo32(cur), (uint32_t)TILE);
+        if (nx < OVF_CHUNK) P.fill[ob][nx] = 0u;
+        // (a chunk past the pool was handed out but not written to: put_flow flags a lost flow)
+        sm.cursor = pack_cursor(NO_CHUNK, 0);
+        sm.next_chunk = NO_CHUNK;
     }
 }
 
-// Writes the flows marked keep[i] (per thread, IPT slots) to the output pool: staged in
-// shared memory at the scanned offsets, then written out contiguously.
+// Writes one flow to slot p of a span (or records the overflow).
 template <typename W>
-__device__ __forceinline__ void write_flows(const Params<W> &P, int ob, Counters *C, const bool (&keep)[IPT],
-                                            const uint32_t (&e)[IPT], const int32_t (&q)[IPT],
-                                            const int32_t (&t)[IPT], uint32_t pos, uint32_t total, Smem &sm,
-                                            const uint32_t *s_base)
+__device__ __forceinline__ void put_flow(const Params<W> &P, int ob, Counters *C, const Span &sp, uint32_t p,
+                                         uint32_t e, int32_t q, int32_t t)
 {
-#pragma unroll
-    for (int i = 0; i < IPT; i++)
-        if (keep[i]) {
-            sm.out_ed[pos] = e[i];
-            sm.out_qa[pos] = q[i];
-            sm.out_ta[pos] = t[i];
-            pos++;
-        }
-    __syncthreads();
-    const uint32_t base = s_base[0];
-    if (total) {
-        if ((unsigned long long)base + total > P.pool_cap) {
-            if (threadIdx.x == 0) atomicExch(&C->overflow, 1u);
-        } else {
-            uint32_t *oe = P.ed[ob];
-            int32_t *oq = P.qa[ob], *ot = P.ta[ob];
-            for (uint32_t j = threadIdx.x; j < total; j += TPB) {
-                oe[base + j] = sm.out_ed[j];
-                oq[base + j] = sm.out_qa[j];
-                ot[base + j] = sm.out_ta[j];
-            }
-        }
+    uint32_t idx;
+    if (span_slot(sp, p, idx)) {
+        P.ed[ob][idx] = e;
+        P.qa[ob][idx] = q;
+        P.ta[ob][idx] = t;
+    } else {
+        atomicExch(&C->overflow, 1u);
     }
-    __syncthreads();
 }
 
 // ---------------------------------------------------------------- the sweep
@@ -448,93 +521,169 @@ __device__ __forceinline__ void write_flows(const Params<W> &P, int ob, Counters
 // One pass over the flow pool (Steps 1-3 and 7-9 of the paper).  For every flow:
 //   dead    if qa <= label[dst] (labels of the end of the previous cycle): dropped;
 //   arrives if it is live and ta == Tg: offers (qa, ~(src*8+dir)) to dst with a 64-bit
-//           atomic max (no return value needed) and is listed as a candidate; the launch
-//           phase finds, for each improved vertex, the one candidate that won;
+//           atomic max (no return value needed) and is listed as a candidate in this
+//           CTA's region; the launch phase finds, for each improved vertex, the one
+//           candidate that won;
 //   survives otherwise: copied to the output pool.
-// Pool tiles arrive by bulk copies into two shared-memory stages: while a tile is
-// processed the next one is already in flight.  With TRACE, live flows set their source's
+// Pool chunks (one tile each) arrive by bulk copies into two shared-memory stages; the
+// warps work through their slices of a tile independently (no block barrier in the
+// loop): the last warp to finish reading a stage starts the copy of the tile after next
+// into it, and each warp compacts its survivors and arrivals with ballots and claims
+// output room with one shared-memory atomic.  With TRACE, live flows set their source's
 // bit in srcbits (counted by the launch phase).
-// Returns false if a copy wait timed out (ctl->err set).
+// The CTA's output cursor must be open.  Returns false (uniformly across the CTA) if a
+// bounded wait gave up (ctl->err set).
 #ifndef CSP_PHASE_INLINE
 #define CSP_PHASE_INLINE __forceinline__
 #endif
 
 template <int D, typename W, bool TRACE>
-__device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_in, int Tg, Counters *C, LocalStats &st,
-                      Smem &sm, uint32_t (&parity)[2], uint32_t *s_warp, uint32_t *s_base)
+__device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_tiles, int Tg, Counters *C,
+                                       LocalStats &st, Smem &sm, uint32_t (&parity)[NSTAGE], uint32_t cand_base,
+                                       uint32_t cand_cap)
 {
     const int ob = ib ^ 1;
     const uint32_t G = g.size;
-    const uint32_t n_tiles = (n_in + TILE - 1) / TILE;
-    if (threadIdx.x == 0 && g.rank < n_tiles) {
-        fence_proxy_async_global();  // pool written by ordinary stores in the previous pass
-        issue_tile(P, sm, 0, ib, g.rank, n_in);
-        if (g.rank + G < n_tiles) issue_tile(P, sm, 1, ib, g.rank + G, n_in);
+    const uint32_t n_chunks = P.pool_cap / (uint32_t)TILE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; s++) sm.read_cnt[s] = 0;
+        sm.n_cand = 0;
+        sm.fail = 0;
+        if (g.rank < n_tiles) fence_proxy_async_global();  // pool written by ordinary stores in the previous pass
+        for (int s = 0; s < NSTAGE; s++)
+            if (g.rank + s * G < n_tiles) issue_tile(P, sm, s, ib, g.rank + s * G);
     }
+    __syncthreads();
+    bool ok = true;
     uint32_t k = 0;
-    for (uint32_t tile = g.rank; tile < n_tiles; tile += G, k++) {
-        const int s = (int)(k & 1u);
-        if (!wait_stage(sm, s, parity[s], P.ctl)) return false;
-        parity[s] ^= 1u;
-        const uint32_t base = tile * (uint32_t)TILE;
+    // software pipeline per warp: the label gathers of the next tile are in flight while
+    // the current tile is classified and written out
+    uint32_t eN[IPT], nfN = 0;
+    int32_t LN[IPT];
+    if (g.rank < n_tiles) {
+        ok = wait_stage_warp(sm, 0, parity[0]);
+        parity[0] ^= 1u;
+        nfN = sm.stage_fill[0];
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
+            eN[i] = j < nfN ? sm.in_ed[0][j] : 0u;
+            LN[i] = j < nfN ? __ldcg(P.label + (eN[i] >> 3)) : INT_MAX;
+        }
+    }
+    int s = 0;  // stage of the current tile (k mod NSTAGE)
+    for (uint32_t tile = g.rank; ok && tile < n_tiles; tile += G, k++, s = s + 1 == NSTAGE ? 0 : s + 1) {
+        const int sn = s + 1 == NSTAGE ? 0 : s + 1;  // stage of the next tile
+        const uint32_t nfill = nfN;
         uint32_t e[IPT];
-        int32_t q[IPT], t[IPT], L[IPT];
-        bool keep[IPT], arr[IPT];
+        int32_t L[IPT];
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
-            const uint32_t j = i * TPB + threadIdx.x;
-            const bool in = base + j < n_in;
-            e[i] = in ? sm.in_ed[s][j] : 0u;
-            q[i] = in ? sm.in_qa[s][j] : 0;
-            t[i] = in ? sm.in_ta[s][j] : 0;
+            e[i] = eN[i];
+            L[i] = LN[i];
         }
-        __syncthreads();  // stage s fully read: refill it with tile + 2G
-        if (threadIdx.x == 0 && tile + 2 * G < n_tiles) {
-            fence_proxy_async_smem();
-            issue_tile(P, sm, s, ib, tile + 2 * G, n_in);
-        }
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            L[i] = INT_MAX;
-            if (base + i * TPB + threadIdx.x < n_in) L[i] = __ldcg(P.label + (e[i] >> 3));
-        }
-        uint32_t nk = 0, nt = 0;
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            keep[i] = arr[i] = false;
-            if (q[i] <= L[i]) continue;  // dead (or padding): removed
-            st.live++;
-            const uint32_t dst = e[i] >> 3;
-            if (TRACE) {
-                const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(P.stride, e[i] & 7u));
-                atomicOr(P.srcbits + (src >> 5), 1u << (src & 31));
+        if (tile + G < n_tiles) {  // next tile: wait for its stage, start its gathers
+            if (!wait_stage_warp(sm, sn, parity[sn])) {
+                ok = false;
+                break;
             }
-            if (t[i] == Tg) {
-                const unsigned long long key =
-                    ((unsigned long long)(uint32_t)q[i] << 32) | arrival_code<D>(P.stride, e[i]);
-                atomicMax(P.offer + dst, key);
-                arr[i] = true;
-                nt++;
-            } else {
-                keep[i] = true;
-                nk++;
-                st.min_ta = min(st.min_ta, t[i]);
+            parity[sn] ^= 1u;
+            nfN = sm.stage_fill[sn];
+#pragma unroll
+            for (int i = 0; i < IPT; i++) {
+                const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
+                eN[i] = j < nfN ? sm.in_ed[sn][j] : 0u;
+                LN[i] = j < nfN ? __ldcg(P.label + (eN[i] >> 3)) : INT_MAX;
             }
         }
-        uint32_t pk, pt, tk, tt;
-        reserve_tile(nk, nt, C, pk, pt, tk, tt, s_warp, s_base);
-        __syncthreads();  // s_base (written by thread 0) is visible after this barrier
-        if (nt) {
-            const uint32_t cb = s_base[1] + pt;
+        uint32_t bk[IPT], ba[IPT];
+        uint32_t nk = 0, na = 0;
 #pragma unroll
-            for (int i = 0, j = 0; i < IPT; i++)
-                if (arr[i]) {
-                    if (cb + j < P.cand_cap) P.cand[cb + j] = e[i];
-                    else atomicExch(&C->overflow, 1u);
-                    j++;
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
+            const int32_t q = j < nfill ? sm.in_qa[s][j] : 0;
+            bool keep = false, arr = false;
+            if (q > L[i]) {  // live (padding has q = 0 <= INT_MAX)
+                st.live++;
+                const uint32_t dst = e[i] >> 3;
+                if (TRACE) {
+                    const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(P.stride, e[i] & 7u));
+                    atomicOr(P.srcbits + (src >> 5), 1u << (src & 31));
                 }
+                const int32_t t = sm.in_ta[s][j];
+                if (t == Tg) {
+                    const unsigned long long key =
+                        ((unsigned long long)(uint32_t)q << 32) | arrival_code<D>(P.stride, e[i]);
+                    atomicMax(P.offer + dst, key);
+                    arr = true;
+                } else {
+                    keep = true;
+                    st.min_ta = min(st.min_ta, t);
+                }
+            }
+            bk[i] = __ballot_sync(0xffffffffu, keep);
+            ba[i] = __ballot_sync(0xffffffffu, arr);
+            nk += __popc(bk[i]);
+            na += __popc(ba[i]);
         }
-        write_flows(P, ob, C, keep, e, q, t, pk, tk, sm, s_base);
+        if (na) {  // list the arrivals in this CTA's candidate region
+            uint32_t cb = 0;
+            if (lane == 0) cb = atomicAdd(&sm.n_cand, na);
+            cb = __shfl_sync(0xffffffffu, cb, 0);
+            st.cands += lane == 0 ? na : 0u;
+#pragma unroll
+            for (int i = 0; i < IPT; i++) {
+                if ((ba[i] >> lane) & 1u) {
+                    const uint32_t pos = cb + __popc(ba[i] & lt);
+                    if (pos < cand_cap) P.cand[cand_base + pos] = e[i];
+                    else atomicExch(&C->overflow, 1u);
+                }
+                cb += __popc(ba[i]);
+            }
+        }
+        if (nk) {  // survivors to the output pool, in ballot order
+            const Span sp = claim_slots(sm, C, P.ctl, P.fill[ob], nk, n_chunks);
+            uint32_t p = sp.f0;
+            st.written += lane == 0 ? nk : 0u;
+#pragma unroll
+            for (int i = 0; i < IPT; i++) {
+                if ((bk[i] >> lane) & 1u) {
+                    const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
+                    put_flow(P, ob, C, sp, p + __popc(bk[i] & lt), e[i], sm.in_qa[s][j], sm.in_ta[s][j]);
+                }
+                p += __popc(bk[i]);
+            }
+        }
+        // this warp is done with stage s; the last warp refills it with tile + NSTAGE * G
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t done = atomicAdd(&sm.read_cnt[s], 1u);
+            if (done == (uint32_t)NWARP - 1u) {
+                __threadfence_block();
+                sm.read_cnt[s] = 0;
+                if (tile + NSTAGE * G < n_tiles) {
+                    fence_proxy_async_smem();
+                    issue_tile(P, sm, s, ib, tile + NSTAGE * G);
+                }
+            }
+        }
+    }
+    bool pending[NSTAGE];
+    // copies possibly issued but never waited for (only after a give-up): the next NSTAGE tiles
+    for (int q = 0; q < NSTAGE; q++) pending[q] = false;
+    if (!ok) {
+        for (int q = 0; q < NSTAGE; q++)
+            if (g.rank + (k + q) * G < n_tiles) pending[(s + q) % NSTAGE] = true;
+        sm.fail = 1;
+        atomicExch(&P.ctl->err, 1);
+    }
+    __syncthreads();
+    if (sm.fail) {
+        drain_stages(sm, parity, pending);
+        return false;
     }
     return true;
 }
@@ -575,59 +724,50 @@ __device__ __forceinline__ uint32_t launch_mask(const EdgeRecord<W, D> &r, int L
     return mask;
 }
 
-// Appends the flows of mask (per thread, one source vertex v) to the output pool through
-// a block-compacted staging area (the sweep's input stages, free during this phase).
+// Warp-collective: appends the flows of mask (per lane, one source vertex v with label Lv)
+// to the output pool with one shared-memory claim per warp.  Flows are laid out direction
+// by direction (a ballot per direction), so that every store instruction of the warp
+// writes one contiguous run of slots.
 template <typename W, int D>
-__device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters *C, uint32_t v, int Lv,
-                                           const EdgeRecord<W, D> &r, uint32_t mask, int Time, LocalStats &st,
-                                           Smem &sm, uint32_t *s_warp, uint32_t *s_base)
+__device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters *C, Smem &sm, uint32_t v, int Lv,
+                                           const EdgeRecord<W, D> &r, uint32_t mask, int Time, LocalStats &st)
 {
-    static_assert(TPB * 2 * D <= 2 * TILE, "launch staging needs TPB * 2d <= 2 * TILE");
-    uint32_t *stage_ed = &sm.in_ed[0][0];
-    int32_t *stage_qa = &sm.in_qa[0][0], *stage_ta = &sm.in_ta[0][0];
-    const uint32_t nk = __popc(mask);
-    uint32_t pos, pt, total, tt;
-    reserve_tile(nk, 0, C, pos, pt, total, tt, s_warp, s_base);
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t bd[2 * D], total = 0;
 #pragma unroll
-    for (int dir = 0; dir < 2 * D; dir++)
-        if (mask & (1u << dir)) {
+    for (int dir = 0; dir < 2 * D; dir++) {
+        bd[dir] = __ballot_sync(0xffffffffu, (mask >> dir) & 1u);
+        total += __popc(bd[dir]);
+    }
+    if (total == 0) return;
+    const Span sp = claim_slots(sm, C, P.ctl, P.fill[ob], total, P.pool_cap / (uint32_t)TILE);
+    st.written += lane == 0 ? total : 0u;
+    uint32_t p = sp.f0;
+#pragma unroll
+    for (int dir = 0; dir < 2 * D; dir++) {
+        if ((bd[dir] >> lane) & 1u) {
             const uint32_t w = v + dir_offset<D>(P.stride, dir);
             const int t = Time + r.f1(dir);
-            stage_ed[pos] = (w << 3) | (uint32_t)(dir ^ 1);
-            stage_qa[pos] = Lv - r.f2(dir);
-            stage_ta[pos] = t;
-            pos++;
+            put_flow(P, ob, C, sp, p + __popc(bd[dir] & lt), (w << 3) | (uint32_t)(dir ^ 1), Lv - r.f2(dir), t);
             st.min_ta = min(st.min_ta, t);
             st.launched++;
         }
-    __syncthreads();
-    const uint32_t base = s_base[0];
-    if (total) {
-        if ((unsigned long long)base + total > P.pool_cap) {
-            if (threadIdx.x == 0) atomicExch(&C->overflow, 1u);
-        } else {
-            uint32_t *oe = P.ed[ob];
-            int32_t *oq = P.qa[ob], *ot = P.ta[ob];
-            for (uint32_t j = threadIdx.x; j < total; j += TPB) {
-                oe[base + j] = stage_ed[j];
-                oq[base + j] = stage_qa[j];
-                ot[base + j] = stage_ta[j];
-            }
-        }
+        p += __popc(bd[dir]);
     }
-    __syncthreads();
 }
 
-// One thread per arrival candidate.  The candidate whose code equals the final offer word
-// of its destination v is the winner: v improved this cycle (Step 2).  The winner commits
-// the label (Step 8), records v if it is in B (Algorithm 2), and starts a flow on every
-// edge (v, w) with Label(v) - f2 > Label(w) under the labels at the end of this cycle
-// (Steps 4-5; a flow on an edge that already carries water is the paper's phantom).
-// Its loads (offer[v], the edge record, the 2d neighbour labels) are issued together.
-// With TRACE, also counts (and clears) the source bitmap filled by the sweep.
+// One thread per arrival candidate of this CTA's region.  The candidate whose code equals
+// the final offer word of its destination v is the winner: v improved this cycle (Step 2).
+// The winner commits the label (Step 8), records v if it is in B (Algorithm 2), and starts
+// a flow on every edge (v, w) with Label(v) - f2 > Label(w) under the labels at the end of
+// this cycle (Steps 4-5; a flow on an edge that already carries water is the paper's
+// phantom).  Its loads (offer[v], the edge record, the 2d neighbour labels) are issued
+// together.  Warps work independently.  With TRACE, also counts (and clears) the source
+// bitmap filled by the sweep.
 template <int D, typename W, bool TRACE>
-__device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int ob, uint32_t n_cand, int Time, Counters *C, LocalStats &st,
-                       Smem &sm, uint32_t *s_warp, uint32_t *s_base)
+__device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int ob, uint32_t cand_base, uint32_t n_cand,
+                                        int Time, Counters *C, LocalStats &st, Smem &sm)
 {
     const uint32_t V = (uint32_t)P.V;
     if (TRACE) {
@@ -640,13 +780,14 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
             }
         }
     }
-    for (uint32_t base = g.rank * TPB; base < n_cand; base += g.size * TPB) {
-        const uint32_t j = base + threadIdx.x;
+    const uint32_t wbase = (threadIdx.x >> 5) * 32u;
+    for (uint32_t base = wbase; base < n_cand; base += TPB) {
+        const uint32_t j = base + (threadIdx.x & 31);
         uint32_t v = 0, mask = 0;
         int Lv = 0;
         EdgeRecord<W, D> r{};
         if (j < n_cand) {
-            const uint32_t ec = __ldcg(P.cand + j);
+            const uint32_t ec = __ldcg(P.cand + cand_base + j);
             v = ec >> 3;
             const uint32_t code = arrival_code<D>(P.stride, ec);
             const unsigned long long ov = __ldcg(P.offer + v);
@@ -663,19 +804,20 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
                 mask = launch_mask<W, D>(r, Lv, Lw);
             }
         }
-        emit_flows<W, D>(P, ob, C, v, Lv, r, mask, Time, st, sm, s_warp, s_base);
+        emit_flows<W, D>(P, ob, C, sm, v, Lv, r, mask, Time, st);
     }
 }
 
 // Seed launch (Algorithm 3): water of quality M leaves every source a in A (listed in
 // cand as plain vertex ids, label M already set) along each edge with M - f2 > Label(w).
 template <int D, typename W>
-__device__ CSP_PHASE_INLINE void seed(const Params<W> &P, const Group &g, uint32_t n_src, Counters *C, LocalStats &st, Smem &sm,
-                     uint32_t *s_warp, uint32_t *s_base)
+__device__ CSP_PHASE_INLINE void seed(const Params<W> &P, const Group &g, uint32_t n_src, Counters *C, LocalStats &st,
+                                      Smem &sm)
 {
     const uint32_t V = (uint32_t)P.V;
-    for (uint32_t base = g.rank * TPB; base < n_src; base += g.size * TPB) {
-        const uint32_t j = base + threadIdx.x;
+    const uint32_t wbase = g.rank * TPB + (threadIdx.x >> 5) * 32u;
+    for (uint32_t base = wbase; base < n_src; base += g.size * TPB) {
+        const uint32_t j = base + (threadIdx.x & 31);
         uint32_t v = 0, mask = 0;
         EdgeRecord<W, D> r{};
         if (j < n_src) {
@@ -685,7 +827,7 @@ __device__ CSP_PHASE_INLINE void seed(const Params<W> &P, const Group &g, uint32
             neighbour_labels<D>(P.offer, P.stride, V, v, Lw);
             mask = launch_mask<W, D>(r, P.M, Lw);
         }
-        emit_flows<W, D>(P, 0, C, v, P.M, r, mask, 0, st, sm, s_warp, s_base);
+        emit_flows<W, D>(P, 0, C, sm, v, P.M, r, mask, 0, st);
     }
 }
 
@@ -694,8 +836,7 @@ __device__ CSP_PHASE_INLINE void seed(const Params<W> &P, const Group &g, uint32
 __device__ __forceinline__ void init_stage_barriers(Smem &sm)
 {
     if (threadIdx.x == 0) {
-        mbar_init(&sm.mbar[0], 1);
-        mbar_init(&sm.mbar[1], 1);
+        for (int s = 0; s < NSTAGE; s++) mbar_init(&sm.mbar[s], 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -714,13 +855,13 @@ __device__ void write_row(const Params<W> &P, long long row, long long time, lon
 __device__ __forceinline__ void zero_counters(Counters *c)
 {
     c->out_cand = c->live = c->lau_imp = c->xkey = 0;
-    c->n_active = c->overflow = c->abort = 0;
+    c->n_active = c->overflow = c->abort = c->chunks = 0;
     c->min_ta = INT_MAX;
 }
 
 // A snapshot of one pass's counters, read by every CTA after the pass's last barrier.
 struct PassCounts {
-    unsigned int n_out, n_cand, launched, improved, n_active, overflow, abort;
+    unsigned int n_out, n_cand, launched, improved, n_active, overflow, abort, chunks;
     unsigned long long n_live, xkey;
     int min_ta;
 };
@@ -737,6 +878,7 @@ __device__ __forceinline__ PassCounts read_counters(const Counters *c)
         const unsigned long long lv = __ldcg(&c->live), xk = __ldcg(&c->xkey);
         const unsigned int act = __ldcg(&c->n_active), ovf = __ldcg(&c->overflow), ab = __ldcg(&c->abort);
         const int mt = __ldcg(&c->min_ta);
+        s_pc.chunks = __ldcg(&c->chunks);
         s_pc.n_out = lo32(oc);
         s_pc.n_cand = hi32(oc);
         s_pc.launched = lo32(li);
@@ -770,8 +912,8 @@ __device__ __forceinline__ unsigned long long read_shared_u64(const unsigned lon
 // distinct sources listed in cand with their count in the high half of cnt[0].out_cand,
 // and fresh counters.  The group leader writes the result record.
 template <int D, typename W, bool TRACE>
-__device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t (&parity)[2], uint32_t *s_warp,
-                          uint32_t *s_base, unsigned long long &epoch)
+__device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t (&parity)[NSTAGE],
+                          unsigned long long &epoch)
 {
     // epoch: barriers already passed on ctl->bar (updated)
     Control *ctl = P.ctl;
@@ -796,10 +938,18 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
     }
 
     {
+        const uint32_t n_chunks = P.pool_cap / (uint32_t)TILE;
+        const uint32_t cand_cta = P.cand_cap / g.size;  // candidate region of each CTA
+        const uint32_t cand_base = g.rank * cand_cta;
         // seed: water leaves A at Time 0 along every edge that can raise a label
-        LocalStats st{0, 0, 0, 0, INT_MAX};
+        LocalStats st{0, 0, 0, 0, 0, 0, INT_MAX};
         const uint32_t n_src = min(hi32(read_shared_u64(&ctl->cnt[0].out_cand)), P.cand_cap);
-        seed<D, W>(P, g, n_src, &ctl->cnt[0], st, sm, s_warp, s_base);
+        // (the seed adds the flows it writes to the low half of out_cand; the high half keeps n_src)
+        if (threadIdx.x == 0) cursor_open(sm, &ctl->cnt[0], n_chunks, g.rank * TPB < n_src);
+        __syncthreads();
+        seed<D, W>(P, g, n_src, &ctl->cnt[0], st, sm);
+        __syncthreads();
+        cursor_close(P, sm, 0);
         flush_stats(st, &ctl->cnt[0]);
         if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
         const PassCounts c = read_counters(&ctl->cnt[0]);
@@ -812,24 +962,26 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
         }
         max_pool = c.n_out;
         int Tg = c.min_ta;
-        uint32_t n_pool = c.n_out;  // flows in the pool the next sweep reads
+        // pool chunks the next sweep reads (chunks handed out past the pool hold no flow)
+        uint32_t n_tiles = min(c.chunks, n_chunks);
 
         for (long long pass = 1;; pass++) {
             const int ib = (int)((pass - 1) & 1), ob = ib ^ 1;
             Counters *C = &ctl->cnt[ob];
-            const uint32_t n_in = n_pool;
-            LocalStats sa{0, 0, 0, 0, INT_MAX};
-            if (!sweep<D, W, TRACE>(P, g, ib, n_in, Tg, C, sa, sm, parity, s_warp, s_base)) {
+            LocalStats sa{0, 0, 0, 0, 0, 0, INT_MAX};
+            if (threadIdx.x == 0) cursor_open(sm, C, n_chunks, g.rank < n_tiles);
+            if (!sweep<D, W, TRACE>(P, g, ib, n_tiles, Tg, C, sa, sm, parity, cand_base, cand_cta)) {
                 status = ST_BARRIER;
                 goto finish;
             }
             flush_stats(sa, C);
             if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
-            if (leader) zero_counters(&ctl->cnt[ib]);  // everyone has read n_in
+            if (leader) zero_counters(&ctl->cnt[ib]);  // everyone has read the input's counts
             if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
-            LocalStats sb{0, 0, 0, 0, INT_MAX};
-            const uint32_t n_cand = min(hi32(read_shared_u64(&C->out_cand)), P.cand_cap);
-            launch<D, W, TRACE>(P, g, ob, n_cand, Tg, C, sb, sm, s_warp, s_base);
+            LocalStats sb{0, 0, 0, 0, 0, 0, INT_MAX};
+            launch<D, W, TRACE>(P, g, ob, cand_base, min(sm.n_cand, cand_cta), Tg, C, sb, sm);
+            __syncthreads();
+            cursor_close(P, sm, ob);
             flush_stats(sb, C);
             if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
             passes = pass;
@@ -850,15 +1002,20 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                     xkey = c.xkey;
                     if (TRACE) {
                         // the terminal cycle's row: count the flows still alive after it
-                        LocalStats sc{0, 0, 0, 0, INT_MAX};
-                        if (!sweep<D, W, TRACE>(P, g, ob, c.n_out, -1, &ctl->cnt[ib], sc, sm, parity, s_warp, s_base)) {
+                        LocalStats sc{0, 0, 0, 0, 0, 0, INT_MAX};
+                        const uint32_t nt = min(c.chunks, n_chunks);
+                        if (threadIdx.x == 0) cursor_open(sm, &ctl->cnt[ib], n_chunks, g.rank < nt);
+                        if (!sweep<D, W, TRACE>(P, g, ob, nt, -1, &ctl->cnt[ib], sc, sm, parity, cand_base,
+                                                cand_cta)) {
                             status = ST_BARRIER;
                             goto finish;
                         }
                         flush_stats(sc, &ctl->cnt[ib]);
                         if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
-                        LocalStats sd{0, 0, 0, 0, INT_MAX};
-                        launch<D, W, TRACE>(P, g, ob, 0, Time, &ctl->cnt[ib], sd, sm, s_warp, s_base);  // count sources
+                        LocalStats sd{0, 0, 0, 0, 0, 0, INT_MAX};
+                        launch<D, W, TRACE>(P, g, ib, cand_base, 0, Time, &ctl->cnt[ib], sd, sm);  // count sources
+                        __syncthreads();
+                        cursor_close(P, sm, ib);
                         flush_stats(sd, &ctl->cnt[ib]);
                         if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
                         const PassCounts cc = read_counters(&ctl->cnt[ib]);
@@ -878,7 +1035,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                 goto finish;
             }
             max_pool = max(max_pool, c.n_out);
-            n_pool = c.n_out;
+            n_tiles = min(c.chunks, n_chunks);
             Tg = c.min_ta;
             if (P.max_cycles > 0 && cycle >= P.max_cycles) { status = ST_TIMEOUT; goto finish; }
             if (Tg >= TIME_LIMIT) { status = ST_CAPACITY; goto finish; }
@@ -954,7 +1111,7 @@ __device__ bool group_setup_sets(const Params<W> &P, const Group &g, const int64
         for (int b = 0; b < 2; b++) {
             Counters &c = ctl->cnt[b];
             c.out_cand = c.live = c.lau_imp = c.xkey = 0;
-            c.n_active = c.overflow = c.abort = 0;
+            c.n_active = c.overflow = c.abort = c.chunks = 0;
             c.min_ta = INT_MAX;
         }
     }

@@ -45,6 +45,7 @@ struct csp_lattice {
     int64_t cand_cap = 0;
     uint32_t *ed[2] = {nullptr, nullptr};
     int32_t *qa[2] = {nullptr, nullptr}, *ta[2] = {nullptr, nullptr};
+    uint32_t *fill[2] = {nullptr, nullptr};  // slots in use per pool chunk
     csp::Control *ctl = nullptr;
     long long *trace = nullptr;
     int64_t trace_cap = 0;
@@ -53,3 +54,11 @@ struct csp_lattice {
 };
 
 int num_sms(int device);
+
+// Largest group of CTAs one solve may use on a device: the candidate list of a workspace
+// is sized for it (one region per CTA).
+inline int max_group_ctas(int device) { return 4 * num_sms(device); }
+
+// Pool slots a pass may leave unused: each CTA of a group holds one partly filled chunk
+// and one chunk allocated ahead.
+inline int64_t chunk_slack(int64_t group_ctas) { return 2 * group_ctas * (int64_t)csp::TILE; }

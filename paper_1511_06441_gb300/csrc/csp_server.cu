@@ -61,6 +61,7 @@ struct GroupSlot {
     uint32_t *ed[2];
     int32_t *qa[2];
     int32_t *ta[2];
+    uint32_t *fill[2];
     Control *ctl;
     long long *result;  // device copy of the current query's result
     uint32_t *touched;  // vertices whose label left 0 during the current query
@@ -87,10 +88,8 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-    __shared__ uint32_t s_warp[NWARP];
-    __shared__ uint32_t s_base[2];
     init_stage_barriers(sm);
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t parity[NSTAGE] = {};
     const int gid = blockIdx.x / S.group_ctas;
     const Group g{(uint32_t)(blockIdx.x % S.group_ctas), (uint32_t)S.group_ctas};
     const GroupSlot &slot = S.slots[gid];
@@ -107,6 +106,7 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
         P.ed[b] = slot.ed[b];
         P.qa[b] = slot.qa[b];
         P.ta[b] = slot.ta[b];
+        P.fill[b] = slot.fill[b];
     }
     P.pool_cap = slot.pool_cap;
     P.ctl = slot.ctl;
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
         // the slot's labels, offers and B bitmap are all zero here (zeroed at creation and
         // undone after every query), so the set-up touches only A and B
         group_setup_sets<W>(P, g, nullptr, q.A, q.nA, T, epoch, false);
-        run_solve<D, W, false>(P, g, sm, parity, s_warp, s_base, epoch);
+        run_solve<D, W, false>(P, g, sm, parity, epoch);
         if (!group_sync(P.ctl, epoch, g, P.barrier_ns)) break;
         if (g.leader()) {
             ResultSlot &out = S.results[pos % S.ring_size];
@@ -274,9 +274,15 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
     int groups = max_ctas / gc;
     if (opt && opt->max_groups > 0) groups = std::min(groups, opt->max_groups);
     const int64_t V = L->V;
-    int64_t pool = opt && opt->pool_capacity > 0 ? opt->pool_capacity : std::max<int64_t>(1 << 16, V);
-    pool = std::min<int64_t>(pool, (int64_t)std::max(L->flow_bound, 1024ull));
-    const int64_t cand = std::max<int64_t>(V, std::min<int64_t>(2 * L->d * V, pool));
+    // default: max(2^16, V) flows (at most the lattice's flow bound) plus the chunks a pass
+    // may leave part-filled; an explicit capacity is taken as given (rounded up to whole chunks)
+    int64_t pool = opt && opt->pool_capacity > 0
+                       ? opt->pool_capacity
+                       : std::min<int64_t>(std::max<int64_t>(1 << 16, V), (int64_t)std::max(L->flow_bound, 1024ull)) +
+                             chunk_slack(gc);
+    pool = std::min<int64_t>(pool, 0xF0000000ll);
+    pool = (pool + TILE - 1) / TILE * TILE;  // whole chunks
+    const int64_t cand = std::max<int64_t>(V, pool + (int64_t)gc * TILE);  // one region per CTA of a group
     size_t per = 0;
     auto take = [&](size_t bytes) {
         size_t o = per;
@@ -286,9 +292,11 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
     const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
                  o_cand = take(cand * 4), o_ctl = take(sizeof(Control)), o_res = take(R_COUNT * 8),
                  o_touched = take(V * 4), o_tn = take(256);
-    size_t o_pool[2][3];
-    for (int b = 0; b < 2; b++)
+    size_t o_pool[2][3], o_fill[2];
+    for (int b = 0; b < 2; b++) {
         for (int f = 0; f < 3; f++) o_pool[b][f] = take((pool + POOL_PAD) * 4);
+        o_fill[b] = take((pool / TILE + 1) * 4);
+    }
     if (opt && opt->memory_budget > 0) groups = (int)std::max<int64_t>(1, std::min<int64_t>(groups, opt->memory_budget / per));
     s->groups = groups;
     s->group_ctas = gc;
@@ -323,6 +331,7 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
             g.ed[q] = (uint32_t *)(b + o_pool[q][0]);
             g.qa[q] = (int32_t *)(b + o_pool[q][1]);
             g.ta[q] = (int32_t *)(b + o_pool[q][2]);
+            g.fill[q] = (uint32_t *)(b + o_fill[q]);
         }
         g.ctl = (Control *)(b + o_ctl);
         g.result = (long long *)(b + o_res);

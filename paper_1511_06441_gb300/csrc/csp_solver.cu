@@ -107,7 +107,7 @@ __global__ void k_reset(Control *ctl)
         for (int b = 0; b < 2; b++) {
             Counters &c = ctl->cnt[b];
             c.out_cand = c.live = c.lau_imp = c.xkey = 0;
-            c.n_active = c.overflow = c.abort = 0;
+            c.n_active = c.overflow = c.abort = c.chunks = 0;
             c.min_ta = INT_MAX;
         }
         for (int i = 0; i < R_COUNT; i++) ctl->out[i] = 0;
@@ -169,12 +169,10 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_cycle(Params<W> P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-    __shared__ uint32_t s_warp[NWARP];
-    __shared__ uint32_t s_base[2];
     init_stage_barriers(sm);
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t parity[NSTAGE] = {};
     unsigned long long epoch = 0;
-    run_solve<D, W, TRACE>(P, Group{blockIdx.x, gridDim.x}, sm, parity, s_warp, s_base, epoch);
+    run_solve<D, W, TRACE>(P, Group{blockIdx.x, gridDim.x}, sm, parity, epoch);
 }
 
 // ---------------------------------------------------------------- host side
@@ -220,6 +218,7 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
     pool_cap = std::max<int64_t>(pool_cap, L->pool_cap);
     sets_cap = std::max<int64_t>(sets_cap, L->sets_cap);
     if (pool_cap > 0xF0000000ll) pool_cap = 0xF0000000ll;
+    pool_cap = (pool_cap + TILE - 1) / TILE * TILE;  // whole chunks
     const int64_t V = L->V;
     const int64_t trace_cap = L->trace_cap ? L->trace_cap : 1 << 16;
     size_t off = 0;
@@ -228,13 +227,17 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
         off = align_up(off + bytes, 256);
         return o;
     };
-    const int64_t cand_cap = std::max<int64_t>(V, std::min<int64_t>(2 * L->d * V, pool_cap));
+    // candidates: one region per CTA of at least (pool / CTAs + TILE) entries, so that no CTA
+    // can run out of room (a CTA lists at most the flows of its ceil(chunks / CTAs) chunks)
+    const int64_t cand_cap = std::max<int64_t>(V, pool_cap + (int64_t)max_group_ctas(L->device) * TILE);
     const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
                  o_srcbits = take(((V + 31) / 32) * 4), o_cand = take(cand_cap * 4), o_ctl = take(sizeof(Control)),
                  o_trace = take(trace_cap * 24), o_sets = take(sets_cap * 8);
-    size_t o_pool[2][3];
-    for (int b = 0; b < 2; b++)
+    size_t o_pool[2][3], o_fill[2];
+    for (int b = 0; b < 2; b++) {
         for (int f = 0; f < 3; f++) o_pool[b][f] = take((pool_cap + POOL_PAD) * 4);
+        o_fill[b] = take((pool_cap / TILE + 1) * 4);
+    }
     void *ws = nullptr;
     cudaError_t e = cudaMalloc(&ws, off);
     if (e != cudaSuccess) {
@@ -260,6 +263,7 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
         L->ed[k] = (uint32_t *)(b + o_pool[k][0]);
         L->qa[k] = (int32_t *)(b + o_pool[k][1]);
         L->ta[k] = (int32_t *)(b + o_pool[k][2]);
+        L->fill[k] = (uint32_t *)(b + o_fill[k]);
     }
     L->pool_cap = pool_cap;
     CSP_CUDA(cudaMemset(L->ctl, 0, sizeof(Control)));
@@ -269,7 +273,8 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
 int64_t default_pool_cap(const csp_lattice *L)
 {
     const int64_t want = std::max<int64_t>(1 << 20, 16 * L->V);
-    return (int64_t)std::min<unsigned long long>((unsigned long long)want, std::max(L->flow_bound, 1024ull));
+    return (int64_t)std::min<unsigned long long>((unsigned long long)want, std::max(L->flow_bound, 1024ull)) +
+           chunk_slack(max_group_ctas(L->device));
 }
 
 
@@ -308,7 +313,7 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         g_last_error = "persistent kernel does not fit on an SM";
         return CSP_ERR_CUDA;
     }
-    const int max_ctas = per_sm * sms;
+    const int max_ctas = std::min(per_sm * sms, max_group_ctas(L->device));
     int ctas = opt && opt->ctas > 0 ? opt->ctas : (int)std::min<int64_t>(max_ctas, std::max<int64_t>(1, V / 4096));
     ctas = std::max(1, std::min(ctas, max_ctas));
 
@@ -331,6 +336,7 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
             P.ed[b] = L->ed[b];
             P.qa[b] = L->qa[b];
             P.ta[b] = L->ta[b];
+            P.fill[b] = L->fill[b];
         }
         P.pool_cap = (unsigned int)L->pool_cap;
         P.ctl = L->ctl;
@@ -339,8 +345,8 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         P.result_dev = (long long *)result_dev;
         P.M = (int)M;
         P.max_cycles = opt ? opt->max_cycles : 0;
-        P.budget_ns = 120ull * 1000000000ull;
-        P.barrier_ns = 4000000000ull;  // no single solve is expected to take minutes
+        P.budget_ns = 1000000000ull * (unsigned long long)(opt && opt->time_limit_s > 0 ? opt->time_limit_s : 120);
+        P.barrier_ns = 4000000000ull;  // one barrier round never takes seconds
     };
     void *args[1];
     if (L->wbytes == 1) {
@@ -549,8 +555,9 @@ static csp_status solve_host(csp_lattice *L, const int64_t *A, int64_t nA, const
         long long o[R_COUNT];
         CSP_CUDA(cudaMemcpyAsync(o, (char *)L->ctl + offsetof(Control, out), sizeof(o), cudaMemcpyDeviceToHost, s));
         CSP_CUDA(cudaStreamSynchronize(s));
-        if (o[R_STATUS] == ST_CAPACITY && L->pool_cap < (int64_t)L->flow_bound && L->pool_cap < 0xF0000000ll) {
-            cap = std::min<int64_t>(2 * L->pool_cap, (int64_t)std::max(L->flow_bound, 1024ull));
+        const int64_t most = (int64_t)std::max(L->flow_bound, 1024ull) + chunk_slack(max_group_ctas(L->device));
+        if (o[R_STATUS] == ST_CAPACITY && L->pool_cap < most && L->pool_cap < 0xF0000000ll) {
+            cap = std::min<int64_t>(2 * L->pool_cap, most);
             continue;  // grow the pool and run again
         }
         out->F1 = o[R_F1];
@@ -712,27 +719,46 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
         V *= extents[k];
         if (V >= (1ll << 28)) return CSP_ERR_INVALID;
     }
-    // carve the static array: per-vertex arrays, control block, then two pool buffers
+    int dev = 0;
+    CSP_CUDA(cudaGetDevice(&dev));
+    const int sms = num_sms(dev);
+    const void *fn = pick_kernel(d, weight_bytes, false);
+    CSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+    int per_sm = 0;
+    CSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TPB, kSmem));
+    if (per_sm < 1) {
+        g_last_error = "persistent kernel does not fit on an SM";
+        return CSP_ERR_CUDA;
+    }
+    const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, V / 4096));
+    // carve the static array: per-vertex arrays, control block, then the candidate list,
+    // the two pool buffers and their chunk fill arrays (sized from what is left)
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
         off = align_up(off + bytes, 256);
         return o;
     };
-    const int64_t cand_cap = 2 * d * V;
     const int rbytes = record_bytes(d, weight_bytes);
     const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
-                 o_cand = take(cand_cap * 4), o_rec = take(V * rbytes), o_ctl = take(sizeof(Control));
-    const size_t kMinPool = 1024;
-    if (off + 2 * 3 * kMinPool * 4 + 3 * 2 * 256 > kStaticBytes) {
+                 o_rec = take(V * rbytes), o_ctl = take(sizeof(Control));
+    // per pool slot: 6 words of the two buffers and one candidate word; candidates get
+    // TILE more entries per CTA; 64 KiB of slack covers alignment, padding and fill arrays
+    const size_t extra = (size_t)ctas * TILE * 4 + (64u << 10);
+    size_t pool_cap = off + extra < kStaticBytes ? (kStaticBytes - off - extra) / 28 : 0;
+    pool_cap = std::min<size_t>(pool_cap, 0xF0000000ull) / TILE * TILE;
+    if (pool_cap < (size_t)TILE || pool_cap + (size_t)ctas * TILE < (size_t)V) {
         g_last_error = "csp_solve_static: lattice too large for the static workspace (" +
                        std::to_string(kStaticBytes >> 20) + " MiB)";
         return CSP_ERR_INVALID;
     }
-    const size_t pool_cap = std::min<size_t>((kStaticBytes - off - 6 * 256) / 24 - POOL_PAD, 0xF0000000ull);
-    size_t o_pool[2][3];
-    for (int b = 0; b < 2; b++)
+    const int64_t cand_cap = (int64_t)pool_cap + (int64_t)ctas * TILE;
+    const size_t o_cand = take(cand_cap * 4);
+    size_t o_pool[2][3], o_fill[2];
+    for (int b = 0; b < 2; b++) {
         for (int f = 0; f < 3; f++) o_pool[b][f] = take((pool_cap + POOL_PAD) * 4);
+        o_fill[b] = take((pool_cap / TILE + 1) * 4);
+    }
     if (off > kStaticBytes) {
         g_last_error = "csp_solve_static: workspace layout exceeds the static array";
         return CSP_ERR_INVALID;
@@ -752,9 +778,6 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
     CSP_CUDA(cudaMemsetAsync(offer, 0, V * 8, s));
     CSP_CUDA(cudaMemsetAsync(isB, 0, ((V + 31) / 32) * 4, s));
     CSP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Control), s));
-    int dev = 0;
-    CSP_CUDA(cudaGetDevice(&dev));
-    const int sms = num_sms(dev);
     k_reset<<<1, 32, 0, s>>>(ctl);
     const long long n[4] = {ext[0], ext[1], ext[2], ext[3]};
     const long long stl[4] = {stride[0], stride[1], stride[2], stride[3]};
@@ -780,15 +803,6 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
         A_dev, nA, isB, V, (int)M, label, offer, cand, ctl);
     CSP_CUDA(cudaGetLastError());
 
-    const void *fn = pick_kernel(d, weight_bytes, false);
-    CSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-    int per_sm = 0;
-    CSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TPB, kSmem));
-    if (per_sm < 1) {
-        g_last_error = "persistent kernel does not fit on an SM";
-        return CSP_ERR_CUDA;
-    }
-    const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, V / 4096));
     Params<uint8_t> P8{};
     Params<uint16_t> P16{};
     auto fill = [&](auto &P) {
@@ -808,6 +822,7 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
             P.ed[q] = (uint32_t *)(b + o_pool[q][0]);
             P.qa[q] = (int32_t *)(b + o_pool[q][1]);
             P.ta[q] = (int32_t *)(b + o_pool[q][2]);
+            P.fill[q] = (uint32_t *)(b + o_fill[q]);
         }
         P.pool_cap = (unsigned int)pool_cap;
         P.ctl = ctl;

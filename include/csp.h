@@ -114,7 +114,9 @@ csp_status csp_reserve(csp_lattice *lat, int64_t pool_capacity);
  *              live flows) after the removals of each cycle, row 0 = after initialisation.
  *              Requesting a trace makes the solve count active vertices (slower).
  *   trace_len  nullable; receives the number of rows the solve produced.  If it exceeds
- *              trace_cap only trace_cap rows were written (status still CSP_OK).
+ *              trace_cap only trace_cap rows were written (status still CSP_OK).  A solve
+ *              stopped by max_cycles or the watchdog (CSP_ERR_TIMEOUT) returns the rows of
+ *              the cycles it completed (rows 0 .. cycles - 1) and their counts in *out.
  * Blocks the calling thread until the result is on the host.
  */
 csp_status csp_solve(csp_lattice *lat, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB,

@@ -8,7 +8,8 @@ The solvers live in ``csp_oracle.c`` (plain C, compiled here with gcc on first u
 
 * :func:`cycle`  - O1, the paper's cycle loop (Algorithm 1, Steps 1-9), with trace;
 * :func:`pareto` - O2, an independent Dijkstra over (vertex, quality) states;
-* :func:`lexmin` - unconstrained lexicographic (F1, F2) Dijkstra (input preparation).
+* :func:`lexmin` - unconstrained lexicographic (F1, F2) Dijkstra (the bound M of the
+  anti-correlated workload, and its answer where that bound does not bind).
 
 Parity unpinned: nothing.  Every output is pinned by the tests against brute force,
 plain Dijkstra, closed forms or the paper's Lemma; see the C file's header.
@@ -198,15 +199,21 @@ def pareto(extents: Sequence[int], f1, f2, A, B, M: int) -> Result:
     return r
 
 
-def lexmin(extents: Sequence[int], f1, f2, A, B):
-    """(F1, F2) of the lexicographically smallest walk from A to B, no weight bound."""
+def lexmin(extents: Sequence[int], f1, f2, A, B, *, full: bool = False):
+    """Lexicographically smallest (F1, F2) over walks from A to B, no weight bound.
+
+    ``full`` adds X and the last edge (x_src, x_dir) under the solver's tie rules; when the
+    returned F2 is below a bound M, (F1, F2, X, x) is the answer for that M.
+    """
     lib = _load()
     ext, f1, f2, A, B = _common(extents, f1, f2, A, B)
-    res = np.zeros(2, np.int64)
+    res = np.zeros(5, np.int64)
     rc = lib.oracle_lexmin(len(ext), _p64(ext), _p32(f1), _p32(f2), _p64(A), A.size, _p64(B), B.size,
                            _p64(res))
     if rc != OK:
         raise OracleError(rc)
+    if full:
+        return tuple(int(x) for x in res)
     return int(res[0]), int(res[1])
 
 

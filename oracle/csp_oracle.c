@@ -16,8 +16,9 @@
  *                    and, on request, the active set at a given time.
  *   oracle_pareto    (O2) a label-setting Dijkstra over (vertex, quality) states with
  *                    dominance pruning; it knows nothing about cycles or flows.
- *   oracle_lexmin    lexicographic (F1, F2) Dijkstra without a weight bound, used only
- *                    to derive the weight bound M of the anti-correlated workload.
+ *   oracle_lexmin    lexicographic (F1, F2) Dijkstra without a weight bound: derives the
+ *                    weight bound M of the anti-correlated workload and, where that
+ *                    bound does not bind, the whole answer (F1, F2, X, x).
  *
  * Lattice: box [0,n_0) x ... x [0,n_{d-1}), vertex id v = sum c_k stride_k with c_0
  * fastest.  f1[k*V+v], f2[k*V+v] are travel time and weight of the edge (v, v+e_k);
@@ -475,6 +476,14 @@ done:
 
 /* Unconstrained lexicographic minimum of (F1, F2) over walks from A to B: a plain
  * Dijkstra on pairs.  res[0] = F1, res[1] = F2 (both -1 if B is unreachable). */
+/*
+ * Lexicographic Dijkstra: walks from A explored in order of (F1, F2), each vertex settled
+ * by its first (lightest among the fastest) state.  res[0..4] = F1, F2, X, x_src, x_dir of
+ * the first settled vertex of B; states of equal (F1, F2) pop by smaller vertex, then
+ * smaller (predecessor, direction), so X and x follow the tie rules of the solver.  When
+ * F2 < M, this is the solver's answer for the bound M: the fastest walks are allowed and
+ * the lightest of them reaches X (Section 1, the problem statement).
+ */
 int oracle_lexmin(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2,
                   const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t *res)
 {
@@ -484,7 +493,7 @@ int oracle_lexmin(int d, const int64_t *ext, const int32_t *f1, const int32_t *f
     const int64_t V = L.V;
     unsigned char *inA = calloc((size_t)V, 1), *inB = calloc((size_t)V, 1), *done_v = calloc((size_t)V, 1);
     heap_t H = {0, 0, 0};
-    res[0] = res[1] = -1;
+    for (int i = 0; i < 5; i++) res[i] = -1;
     if (!inA || !inB || !done_v) {
         rc = OR_OOM;
         goto done;
@@ -504,6 +513,9 @@ int oracle_lexmin(int d, const int64_t *ext, const int32_t *f1, const int32_t *f
         if (inB[s.v]) {
             res[0] = s.t;
             res[1] = -s.q;
+            res[2] = s.v;
+            res[3] = s.src;
+            res[4] = s.dir;
             break;
         }
         for (int dir = 0; dir < 2 * d; dir++) {

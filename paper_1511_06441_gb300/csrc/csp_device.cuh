@@ -991,7 +991,11 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             arrivals += (long long)c.n_cand;
             improved += (long long)c.improved;
             if (c.overflow) { status = ST_CAPACITY; goto finish; }
-            if (c.abort) { status = ST_TIMEOUT; goto finish; }
+            if (c.abort) {  // rows 0 .. cycle - 1 are complete
+                status = ST_TIMEOUT;
+                trace_len = cycle;
+                goto finish;
+            }
             if (c.n_cand > 0) {  // a real cycle at time Tg
                 if (TRACE && leader) write_row(P, cycle, Time, c.n_active, (long long)c.n_live);
                 updates += (long long)c.n_live;
@@ -1037,7 +1041,11 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             max_pool = max(max_pool, c.n_out);
             n_tiles = min(c.chunks, n_chunks);
             Tg = c.min_ta;
-            if (P.max_cycles > 0 && cycle >= P.max_cycles) { status = ST_TIMEOUT; goto finish; }
+            if (P.max_cycles > 0 && cycle >= P.max_cycles) {  // rows 0 .. cycle - 1 are complete
+                status = ST_TIMEOUT;
+                trace_len = cycle;
+                goto finish;
+            }
             if (Tg >= TIME_LIMIT) { status = ST_CAPACITY; goto finish; }
         }
     }

@@ -174,3 +174,62 @@ def test_duplicates_in_A_and_B_are_sets():
     b = oracle.cycle(inst.extents, inst.f1, inst.f2, A2, B2, 300)
     assert a.answer() == b.answer()
     np.testing.assert_array_equal(a.trace, b.trace)
+
+
+# ---------------------------------------------------------------- unconstrained lexicographic optimum
+
+BIG_M = (1 << 31) - 2
+
+
+@pytest.mark.parametrize("seed", range(2000, 2060))
+def test_lexmin_equals_brute_force_without_bound(seed):
+    """With no binding bound the answer is the lexicographic (F1, F2) optimum; brute force
+    over simple paths gives it with the same tie rules for X and x."""
+    inst = _tiny(seed)
+    inst.M = BIG_M
+    F1, X, xs, xd, F2 = brute.brute_force(inst)
+    assert oracle.lexmin(inst.extents, inst.f1, inst.f2, inst.A, inst.B, full=True) == (F1, F2, X, xs, xd)
+
+
+@pytest.mark.parametrize("seed", range(2100, 2140))
+def test_lexmin_is_the_answer_where_the_bound_does_not_bind(seed):
+    """Section 1: if the lightest fastest walk satisfies F2 < M, the cycle loop returns it."""
+    inst = _tiny(seed)
+    F1, F2, X, xs, xd = oracle.lexmin(inst.extents, inst.f1, inst.f2, inst.A, inst.B, full=True)
+    if F1 < 0:
+        return
+    inst.M = F2 + 1 + seed % 7
+    assert oracle.solve_instance(inst).answer() == (F1, X, xs, xd, F2)
+
+
+def _scipy_lexmin(inst):
+    """(F1, F2, X, x_src, x_dir) from scipy's Dijkstra on the composite weight f1 * 2^25 + f2
+    (exact in float64 at these sizes), x by the smallest (predecessor, direction) among the
+    neighbours Y of X with dist(Y) + w(Y, X) = dist(X)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import dijkstra
+    S = float(1 << 25)
+    adj, V = brute.directed_edges(inst.extents, inst.f1, inst.f2)
+    rows, cols, wts = [], [], []
+    for v, es in adj.items():
+        for u, _, t1, w1 in es:
+            rows.append(v)
+            cols.append(u)
+            wts.append(t1 * S + w1)
+    G = csr_matrix((np.array(wts), (np.array(rows), np.array(cols))), shape=(V, V))
+    dist = dijkstra(G, indices=sorted(set(int(a) for a in inst.A)), min_only=True)
+    B = sorted(set(int(b) for b in inst.B))
+    X = min(B, key=lambda b: (dist[b], b))
+    best = None
+    for u, dr, t1, w1 in adj[X]:
+        if dist[u] + (t1 * S + w1) == dist[X]:
+            key = (u, dr ^ 1)  # the edge leaves u towards X in the reverse direction
+            best = key if best is None else min(best, key)
+    F1, F2 = int(dist[X] // S), int(dist[X] % S)
+    return F1, F2, X, best[0], best[1]
+
+
+@pytest.mark.parametrize("side,seed", [(48, 3), (64, 11), (96, 12)])
+def test_lexmin_equals_scipy_dijkstra_on_anticorrelated_lattices(side, seed):
+    inst = synth.workload_anticorrelated(side, seed=seed)
+    assert oracle.lexmin(inst.extents, inst.f1, inst.f2, inst.A, inst.B, full=True) == _scipy_lexmin(inst)

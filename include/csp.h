@@ -249,6 +249,28 @@ csp_status csp_solve_batch(const csp_query *q, int64_t n, const csp_batch_option
 csp_status csp_reconstruct_path(csp_lattice *lat, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB,
                                 int64_t M, const csp_result *res, int64_t *path, int64_t cap, int64_t *len);
 
+/*
+ * The same path as csp_reconstruct_path from ONE solve: the solve records, for every
+ * vertex, the time and winning arrival edge of its first improvement and, in a log, every
+ * improvement pass by pass; a GPU backtrack then walks from (X, F1) along the recorded
+ * edges (the flow on x left Y at F1 - f1(x), when Y improved; and so on back to A).
+ * Repeated application would remove the path vertices found so far; no earlier vertex of
+ * the path is reached sooner with better water through a later one, so the result is the
+ * same path.
+ *   opt           nullable, as for csp_solve.
+ *   log_capacity  improvement records the log may hold (8 bytes each): > 0 that many;
+ *                 0 = a quarter of the free device memory; < 0 = no log (first improvements
+ *                 only, which suffice when every path vertex is reached at its first
+ *                 improvement, e.g. when the bound does not bind).  A path that needs a
+ *                 record the log dropped returns CSP_ERR_CAPACITY.
+ *   res           receives the solve's result (as csp_solve).
+ *   path, cap, len  as for csp_reconstruct_path (A end first; 0 vertices if infeasible).
+ * Allocates and frees its record buffers (8 bytes per vertex plus the log); blocks until done.
+ */
+csp_status csp_reconstruct_fast(csp_lattice *lat, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB,
+                                int64_t M, const csp_options *opt, int64_t log_capacity, csp_result *res,
+                                int64_t *path, int64_t cap, int64_t *len);
+
 /* ------------------------------------------------------------------ serving
  *
  * A resident lattice answering a stream of queries with continuous batching: one

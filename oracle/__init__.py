@@ -57,7 +57,7 @@ def _load():
             lib.oracle_pareto.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
                                           ctypes.c_int64, ctypes.c_int64, i64p]
             lib.oracle_lexmin.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
-                                          ctypes.c_int64, i64p]
+                                          ctypes.c_int64, i64p, i64p, ctypes.c_int64, i64p]
             for f in (lib.oracle_cycle, lib.oracle_pareto, lib.oracle_lexmin):
                 f.restype = ctypes.c_int
             _lib = lib
@@ -199,19 +199,30 @@ def pareto(extents: Sequence[int], f1, f2, A, B, M: int) -> Result:
     return r
 
 
-def lexmin(extents: Sequence[int], f1, f2, A, B, *, full: bool = False):
+def lexmin(extents: Sequence[int], f1, f2, A, B, *, full: bool = False, path: bool = False):
     """Lexicographically smallest (F1, F2) over walks from A to B, no weight bound.
 
     ``full`` adds X and the last edge (x_src, x_dir) under the solver's tie rules; when the
-    returned F2 is below a bound M, (F1, F2, X, x) is the answer for that M.
+    returned F2 is below a bound M, (F1, F2, X, x) is the answer for that M.  ``path``
+    returns ``(F1, F2, X, x_src, x_dir, vertices)`` with the walk itself (A end first): each
+    vertex's settled predecessor, i.e. its own lexicographically smallest prefix.
     """
     lib = _load()
     ext, f1, f2, A, B = _common(extents, f1, f2, A, B)
     res = np.zeros(5, np.int64)
-    rc = lib.oracle_lexmin(len(ext), _p64(ext), _p32(f1), _p32(f2), _p64(A), A.size, _p64(B), B.size,
-                           _p64(res))
-    if rc != OK:
-        raise OracleError(rc)
+    n = np.zeros(1, np.int64)
+    buf = np.zeros(1, np.int64)
+    for _ in range(2):
+        rc = lib.oracle_lexmin(len(ext), _p64(ext), _p32(f1), _p32(f2), _p64(A), A.size, _p64(B), B.size,
+                               _p64(res), _p64(buf) if path else None, buf.size if path else 0,
+                               _p64(n) if path else None)
+        if rc != OK:
+            raise OracleError(rc)
+        if not path or n[0] <= buf.size:
+            break
+        buf = np.zeros(int(n[0]), np.int64)
+    if path:
+        return tuple(int(x) for x in res) + ([int(v) for v in buf[: int(n[0])]] if res[0] >= 0 else None,)
     if full:
         return tuple(int(x) for x in res)
     return int(res[0]), int(res[1])

@@ -484,17 +484,22 @@ done:
  * F2 < M, this is the solver's answer for the bound M: the fastest walks are allowed and
  * the lightest of them reaches X (Section 1, the problem statement).
  */
+/* path (nullable, cap entries): the settled predecessors from X back to A, written A first;
+ * *path_len = its length (> cap: not written). */
 int oracle_lexmin(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2,
-                  const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t *res)
+                  const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t *res,
+                  int64_t *path, int64_t cap, int64_t *path_len)
 {
     lattice_t L;
     int rc = lattice_init(&L, d, ext, f1, f2);
     if (rc) return rc;
     const int64_t V = L.V;
     unsigned char *inA = calloc((size_t)V, 1), *inB = calloc((size_t)V, 1), *done_v = calloc((size_t)V, 1);
+    int64_t *pred = path_len ? malloc((size_t)V * sizeof(int64_t)) : NULL;
     heap_t H = {0, 0, 0};
     for (int i = 0; i < 5; i++) res[i] = -1;
-    if (!inA || !inB || !done_v) {
+    if (path_len) *path_len = 0;
+    if (!inA || !inB || !done_v || (path_len && !pred)) {
         rc = OR_OOM;
         goto done;
     }
@@ -510,12 +515,22 @@ int oracle_lexmin(int d, const int64_t *ext, const int32_t *f1, const int32_t *f
         state_t s = heap_pop(&H);
         if (done_v[s.v]) continue;
         done_v[s.v] = 1;
+        if (pred) pred[s.v] = s.src;
         if (inB[s.v]) {
             res[0] = s.t;
             res[1] = -s.q;
             res[2] = s.v;
             res[3] = s.src;
             res[4] = s.dir;
+            if (pred) {
+                int64_t n = 0;
+                for (int64_t v = s.v; v >= 0; v = pred[v]) n++;
+                *path_len = n;
+                if (path && n <= cap) {
+                    int64_t i = n;
+                    for (int64_t v = s.v; v >= 0; v = pred[v]) path[--i] = v;
+                }
+            }
             break;
         }
         for (int dir = 0; dir < 2 * d; dir++) {
@@ -527,6 +542,6 @@ int oracle_lexmin(int d, const int64_t *ext, const int32_t *f1, const int32_t *f
         }
     }
 done:
-    free(inA); free(inB); free(done_v); free(H.a);
+    free(inA); free(inB); free(done_v); free(H.a); free(pred);
     return rc;
 }

@@ -73,6 +73,8 @@ def lib():
         L.csp_get_labels.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
         L.csp_solve_static.argtypes = [ctypes.c_int, i64p, vp, vp, ctypes.c_int, vp, i64, vp, i64, i64, i64, vp, vp]
         L.csp_reconstruct_path.argtypes = [vp, i64p, i64, i64p, i64, i64, ctypes.POINTER(CspResult), i64p, i64, i64p]
+        L.csp_reconstruct_fast.argtypes = [vp, i64p, i64, i64p, i64, i64, ctypes.POINTER(CspOptions), i64,
+                                           ctypes.POINTER(CspResult), i64p, i64, i64p]
         L.csp_reconstruct_path.restype = ctypes.c_int
         for f in ("csp_create_lattice", "csp_upload_weights", "csp_reserve", "csp_solve", "csp_solve_async",
                   "csp_get_labels", "csp_solve_static"):
@@ -228,6 +230,25 @@ class Lattice:
                                           int(M), ctypes.byref(res) if res is not None else None,
                                           out.ctypes.data_as(i64p), cap, ctypes.byref(n)), "csp_reconstruct_path")
         return out[: n.value].copy() if n.value else None
+
+    def reconstruct_fast(self, A, B, M: int, *, log_capacity: int = 0, cap: int = 1 << 20, max_cycles: int = 0,
+                         ctas: int = 0, time_limit_s: int = 0, stream=None):
+        """``csp_reconstruct_fast``: one recorded solve and a GPU backtrack.
+
+        Returns ``(path, result)``; ``path`` is None if infeasible.  ``log_capacity`` < 0 keeps
+        first improvements only (enough when the bound does not bind along the path).
+        """
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
+        B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
+        opt = options(max_cycles, 0, ctas, stream, time_limit_s=time_limit_s)
+        res = CspResult()
+        out = np.zeros(cap, np.int64)
+        n = ctypes.c_int64(0)
+        _check(lib().csp_reconstruct_fast(self._h, A.ctypes.data_as(i64p), A.size, B.ctypes.data_as(i64p), B.size,
+                                          int(M), ctypes.byref(opt), int(log_capacity), ctypes.byref(res),
+                                          out.ctypes.data_as(i64p), cap, ctypes.byref(n)), "csp_reconstruct_fast")
+        r = Result(*[int(getattr(res, name)) for name, _ in CspResult._fields_], status=0)
+        return (out[: n.value].copy() if n.value else None), r
 
     def labels(self) -> np.ndarray:
         out = np.zeros(self.V, np.int32)

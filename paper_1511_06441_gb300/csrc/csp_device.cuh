@@ -129,6 +129,15 @@ struct Params {
     unsigned long long barrier_ns;  // longest wait at one barrier before giving up
     uint32_t *touched;              // nullable: vertices whose label left 0 are appended here
     unsigned int *touched_n;        // its length
+    // Improvement record for path reconstruction (all nullable):
+    int32_t *first_t;               // [V] time of the vertex's first improvement
+    uint32_t *first_code;           // [V] winning arrival code ~(src * 8 + dir) of that improvement
+    uint2 *log;                     // every improvement (v, code), pass by pass
+    unsigned long long log_cap;     // records that fit in log
+    unsigned long long *log_n;      // records produced (may exceed log_cap: the rest were dropped)
+    int32_t *pass_time;             // [pass_cap] Time of each pass
+    unsigned long long *pass_off;   // [pass_cap + 1] first log record of each pass
+    long long pass_cap;
 };
 
 // Dynamic shared memory of the cycle kernel: NSTAGE input stages filled by bulk copies,
@@ -783,25 +792,44 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
     const uint32_t wbase = (threadIdx.x >> 5) * 32u;
     for (uint32_t base = wbase; base < n_cand; base += TPB) {
         const uint32_t j = base + (threadIdx.x & 31);
-        uint32_t v = 0, mask = 0;
+        uint32_t v = 0, mask = 0, code = 0;
         int Lv = 0;
+        bool won = false;
         EdgeRecord<W, D> r{};
         if (j < n_cand) {
             const uint32_t ec = __ldcg(P.cand + cand_base + j);
             v = ec >> 3;
-            const uint32_t code = arrival_code<D>(P.stride, ec);
+            code = arrival_code<D>(P.stride, ec);
             const unsigned long long ov = __ldcg(P.offer + v);
             r = load_record<W, D>(P.rec, v);
             int Lw[2 * D];
             neighbour_labels<D>(P.offer, P.stride, V, v, Lw);
             if (lo32(ov) == code) {  // the winning arrival at v
+                won = true;
                 Lv = (int)hi32(ov);
-                if (P.touched && __ldcg(P.label + v) == 0) P.touched[atomicAdd(P.touched_n, 1u)] = v;
+                if ((P.touched || P.first_t) && __ldcg(P.label + v) == 0) {  // the first improvement of v
+                    if (P.touched) P.touched[atomicAdd(P.touched_n, 1u)] = v;
+                    if (P.first_t) {
+                        P.first_t[v] = Time;
+                        P.first_code[v] = code;
+                    }
+                }
                 P.label[v] = Lv;
                 st.improved++;
                 if (in_set(P.isB, v))
                     atomicMax(&C->xkey, ((unsigned long long)(uint32_t)Lv << 32) | (0xffffffffu - v));
                 mask = launch_mask<W, D>(r, Lv, Lw);
+            }
+        }
+        if (P.log) {  // every improvement, in this pass's segment of the log
+            const uint32_t bw = __ballot_sync(0xffffffffu, won);
+            if (bw) {
+                const int lane = threadIdx.x & 31;
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(P.log_n, (unsigned long long)__popc(bw));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const unsigned long long i = base + __popc(bw & ((1u << lane) - 1u));
+                if (won && i < P.log_cap) P.log[i] = make_uint2(v, code);
             }
         }
         emit_flows<W, D>(P, ob, C, sm, v, Lv, r, mask, Time, st);
@@ -977,6 +1005,10 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             flush_stats(sa, C);
             if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
             if (leader) zero_counters(&ctl->cnt[ib]);  // everyone has read the input's counts
+            if (leader && P.log && pass < P.pass_cap) {  // this pass's log segment starts here
+                P.pass_time[pass] = Tg;
+                P.pass_off[pass] = *(volatile unsigned long long *)P.log_n;
+            }
             if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
             LocalStats sb{0, 0, 0, 0, 0, 0, INT_MAX};
             launch<D, W, TRACE>(P, g, ob, cand_base, min(sm.n_cand, cand_cta), Tg, C, sb, sm);
@@ -1051,6 +1083,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
     }
 
 finish:
+    if (leader && P.log && passes + 1 <= P.pass_cap) P.pass_off[passes + 1] = *(volatile unsigned long long *)P.log_n;
     if (leader) {
         long long *o = ctl->out;
         for (int i = 0; i < R_COUNT; i++) o[i] = -1;

@@ -55,6 +55,18 @@ struct csp_lattice {
 
 int num_sms(int device);
 
+// Device buffers that record improvements for path reconstruction (see Params).
+struct ReconLog {
+    int32_t *first_t = nullptr;
+    uint32_t *first_code = nullptr;
+    uint2 *log = nullptr;
+    unsigned long long log_cap = 0;
+    unsigned long long *log_n = nullptr;
+    int32_t *pass_time = nullptr;
+    unsigned long long *pass_off = nullptr;
+    long long pass_cap = 0;
+};
+
 // Largest group of CTAs one solve may use on a device: the candidate list of a workspace
 // is sized for it (one region per CTA).
 inline int max_group_ctas(int device) { return 4 * num_sms(device); }

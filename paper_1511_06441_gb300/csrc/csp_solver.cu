@@ -162,6 +162,101 @@ __global__ void k_mark_A(const int64_t *A, long long nA, const uint32_t *isB, lo
     }
 }
 
+// Path reconstruction from an improvement record (one CTA).  A walk that reaches X at
+// time F1 with the solve's answer entered X along x = (Y, dir); the flow on x left Y at
+// t_Y = F1 - f1(x), when Y improved, so Y's improvement at t_Y names the edge that
+// entered Y, and so on back to a source of A (time 0).  The improvement at t_Y is Y's
+// first one when first_t[Y] = t_Y; otherwise it is looked up in the log segment of the
+// pass run at t_Y (a vertex improves at most once per pass).  This is the path repeated
+// application (Section 1) finds: earlier vertices on it never reach later ones sooner
+// with better water, so removing them changes nothing.
+// out[0] = path length (X first), out[1] = status (0, or CSP_ERR_CAPACITY if a needed log
+// record was dropped, or CSP_ERR_CUDA if the record is inconsistent).
+template <typename W>
+__global__ void k_backtrack(const W *f1, long long V, int d, int s0, int s1, int s2, int s3, long long X, long long F1,
+                            uint32_t code0, const int32_t *first_t, const uint32_t *first_code, const uint2 *log,
+                            unsigned long long log_cap, const int32_t *pass_time, const unsigned long long *pass_off,
+                            long long n_pass, long long *path, long long cap, long long *out)
+{
+    __shared__ long long s_v, s_t, s_n;
+    __shared__ unsigned long long s_lo, s_hi;
+    __shared__ uint32_t s_code;
+    __shared__ int s_mode, s_status, s_found;
+    const int stride[4] = {s0, s1, s2, s3};
+    if (threadIdx.x == 0) {
+        s_v = X;
+        s_t = F1;
+        s_code = code0;
+        s_n = 1;
+        if (cap > 0) path[0] = X;
+        s_status = ST_CUDA;  // until the walk reaches A
+    }
+    __syncthreads();
+    for (long long step = 0; step <= F1; step++) {
+        if (threadIdx.x == 0) {
+            s_mode = 0;  // 0: next step, 1: scan the log, 2: stop
+            const uint32_t sd = 0xffffffffu - s_code;
+            const long long src = sd >> 3;
+            const int dir = (int)(sd & 7u), k = dir >> 1;
+            const long long lo = (dir & 1) ? src - stride[k] : src;  // lower end of the edge
+            const long long f = (src < V && k < d && lo >= 0 && lo < V) ? (long long)f1[(long long)k * V + lo] : 0;
+            const long long ty = s_t - f;
+            if (s_n < cap) path[s_n] = src;
+            s_n++;
+            if (f <= 0 || ty < 0) {
+                s_mode = 2;  // inconsistent record
+            } else if (ty == 0) {
+                s_status = ST_OK;  // src is a source: water leaves A at time 0 only
+                s_mode = 2;
+            } else if (__ldcg(first_t + src) == (int32_t)ty) {
+                s_code = __ldcg(first_code + src);
+                s_v = src;
+                s_t = ty;
+            } else {
+                long long a = 1, b = n_pass;  // pass_time[1 .. n_pass] increases
+                while (a < b) {
+                    const long long m = (a + b) / 2;
+                    if (__ldcg(pass_time + m) < ty) a = m + 1;
+                    else b = m;
+                }
+                if (n_pass < 1 || __ldcg(pass_time + a) != (int32_t)ty) {
+                    s_mode = 2;
+                } else {
+                    s_lo = __ldcg(pass_off + a);
+                    s_hi = __ldcg(pass_off + a + 1);
+                    if (s_hi > log_cap) {
+                        s_status = ST_CAPACITY;
+                        s_mode = 2;
+                    } else {
+                        s_v = src;
+                        s_t = ty;
+                        s_found = 0;
+                        s_mode = 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_mode == 2) break;
+        if (s_mode == 1) {
+            for (unsigned long long i = s_lo + threadIdx.x; i < s_hi; i += blockDim.x) {
+                const uint2 r = log[i];
+                if ((long long)r.x == s_v) {
+                    s_code = r.y;
+                    s_found = 1;
+                }
+            }
+            __syncthreads();
+            if (!s_found) break;  // (uniform: read after the barrier) inconsistent record
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = s_n;
+        out[1] = s_status;
+    }
+}
+
 // ---------------------------------------------------------------- the persistent kernel
 
 template <int D, typename W, bool TRACE>
@@ -281,9 +376,10 @@ int64_t default_pool_cap(const csp_lattice *L)
 // Enqueues one solve (set-up kernels + persistent kernel) on stream s.
 csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB, int64_t M,
                          const csp_options *opt, long long *trace_dev, int64_t trace_cap, int64_t *result_dev,
-                         cudaStream_t s, const int64_t *R_dev = nullptr, int64_t nR = 0)
+                         cudaStream_t s, const int64_t *R_dev = nullptr, int64_t nR = 0, const ReconLog *rl = nullptr)
 {
     const int64_t V = L->V;
+    if (rl && rl->log_n) CSP_CUDA(cudaMemsetAsync(rl->log_n, 0, sizeof(unsigned long long), s));
     CSP_CUDA(cudaMemsetAsync(L->label, 0, V * 4, s));
     CSP_CUDA(cudaMemsetAsync(L->offer, 0, V * 8, s));
     CSP_CUDA(cudaMemsetAsync(L->isB, 0, ((V + 31) / 32) * 4, s));
@@ -347,6 +443,16 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         P.max_cycles = opt ? opt->max_cycles : 0;
         P.budget_ns = 1000000000ull * (unsigned long long)(opt && opt->time_limit_s > 0 ? opt->time_limit_s : 120);
         P.barrier_ns = 4000000000ull;  // one barrier round never takes seconds
+        if (rl) {
+            P.first_t = rl->first_t;
+            P.first_code = rl->first_code;
+            P.log = rl->log;
+            P.log_cap = rl->log_cap;
+            P.log_n = rl->log_n;
+            P.pass_time = rl->pass_time;
+            P.pass_off = rl->pass_off;
+            P.pass_cap = rl->pass_cap;
+        }
     };
     void *args[1];
     if (L->wbytes == 1) {
@@ -384,7 +490,7 @@ csp_status check_sets_host(const csp_lattice *L, const int64_t *A, int64_t nA, c
 
 static csp_status solve_host(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
                              const csp_options *opt, csp_result *out, int64_t *trace, int64_t trace_cap,
-                             int64_t *trace_len, const int64_t *R, int64_t nR);
+                             int64_t *trace_len, const int64_t *R, int64_t nR, const ReconLog *rl = nullptr);
 
 extern "C" {
 
@@ -525,7 +631,7 @@ csp_status csp_solve(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t
 // from the graph (a reconstruction step).
 static csp_status solve_host(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
                       const csp_options *opt, csp_result *out, int64_t *trace, int64_t trace_cap, int64_t *trace_len,
-                      const int64_t *R, int64_t nR)
+                      const int64_t *R, int64_t nR, const ReconLog *rl)
 {
     if (!L || !out || M >= (1ll << 31) || M < -(1ll << 31) + 1) return CSP_ERR_INVALID;
     if (trace && trace_cap < 0) return CSP_ERR_INVALID;
@@ -550,7 +656,7 @@ static csp_status solve_host(csp_lattice *L, const int64_t *A, int64_t nA, const
         CSP_CUDA(cudaMemcpyAsync(L->sets + nA, B, nB * 8, cudaMemcpyHostToDevice, s));
         if (nR > 0) CSP_CUDA(cudaMemcpyAsync(L->sets + nA + nB, R, nR * 8, cudaMemcpyHostToDevice, s));
         st = enqueue_solve(L, L->sets, nA, L->sets + nA, nB, M, opt, trace ? L->trace : nullptr,
-                           trace ? L->trace_cap : 0, nullptr, s, nR > 0 ? L->sets + nA + nB : nullptr, nR);
+                           trace ? L->trace_cap : 0, nullptr, s, nR > 0 ? L->sets + nA + nB : nullptr, nR, rl);
         if (st != CSP_OK) return st;
         long long o[R_COUNT];
         CSP_CUDA(cudaMemcpyAsync(o, (char *)L->ctl + offsetof(Control, out), sizeof(o), cudaMemcpyDeviceToHost, s));
@@ -638,6 +744,95 @@ csp_status csp_reconstruct_path(csp_lattice *L, const int64_t *A, int64_t nA, co
     if (*len > cap) return CSP_ERR_CAPACITY;
     for (int64_t i = 0; i < *len; i++) path[i] = found[*len - 1 - i];
     return CSP_OK;
+}
+
+csp_status csp_reconstruct_fast(csp_lattice *L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                                const csp_options *opt, int64_t log_capacity, csp_result *res, int64_t *path,
+                                int64_t cap, int64_t *len)
+{
+    if (!L || !A || !B || nA < 1 || nB < 1 || !len || !res || (cap > 0 && !path)) return CSP_ERR_INVALID;
+    *len = 0;
+    const int64_t V = L->V;
+    const long long pass_cap = 1ll << 21;
+    int64_t lc = 0;
+    if (log_capacity > 0) {
+        lc = log_capacity;
+    } else if (log_capacity == 0) {
+        size_t free_b = 0, total_b = 0;
+        CSP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        lc = (int64_t)std::min<size_t>(free_b / 4 / sizeof(uint2), 0xffffffffull);
+    }
+    // one allocation: first-improvement arrays, log counter, pass table, result words, log
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_ft = take(V * 4), o_fc = take(V * 4), o_n = take(8), o_pt = take((pass_cap + 1) * 4),
+                 o_po = take((pass_cap + 2) * 8), o_out = take(16), o_path = take((size_t)std::max<int64_t>(cap, 1) * 8),
+                 o_log = take((size_t)lc * sizeof(uint2));
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMalloc(reconstruction record)");
+    }
+    char *b = (char *)buf;
+    ReconLog rl;
+    rl.first_t = (int32_t *)(b + o_ft);
+    rl.first_code = (uint32_t *)(b + o_fc);
+    rl.log = lc > 0 ? (uint2 *)(b + o_log) : nullptr;
+    rl.log_cap = (unsigned long long)lc;
+    rl.log_n = (unsigned long long *)(b + o_n);
+    rl.pass_time = (int32_t *)(b + o_pt);
+    rl.pass_off = (unsigned long long *)(b + o_po);
+    rl.pass_cap = pass_cap;
+    csp_status st = solve_host(L, A, nA, B, nB, M, opt, res, nullptr, 0, nullptr, nullptr, 0, &rl);
+    if (st == CSP_OK && res->F1 >= 0) {
+        cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
+        const long long n_pass = std::min<long long>(res->passes, pass_cap - 1);
+        const uint32_t code0 = 0xffffffffu - (uint32_t)(res->x_src * 8 + res->x_dir);
+        long long *dpath = (long long *)(b + o_path), *dout = (long long *)(b + o_out);
+        if (L->wbytes == 1)
+            k_backtrack<uint8_t><<<1, 512, 0, s>>>((const uint8_t *)L->f1, V, L->d, L->stride[0], L->stride[1],
+                                                   L->stride[2], L->stride[3], res->X, res->F1, code0, rl.first_t,
+                                                   rl.first_code, rl.log, rl.log_cap, rl.pass_time, rl.pass_off, n_pass,
+                                                   dpath, cap, dout);
+        else
+            k_backtrack<uint16_t><<<1, 512, 0, s>>>((const uint16_t *)L->f1, V, L->d, L->stride[0], L->stride[1],
+                                                    L->stride[2], L->stride[3], res->X, res->F1, code0, rl.first_t,
+                                                    rl.first_code, rl.log, rl.log_cap, rl.pass_time, rl.pass_off,
+                                                    n_pass, dpath, cap, dout);
+        long long o[2] = {0, 0};
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(o, dout, sizeof(o), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(buf);
+            return cuda_fail(e, "csp_reconstruct_fast");
+        }
+        *len = o[0];
+        if (o[1] == ST_CAPACITY) {
+            set_error("csp_reconstruct_fast: the improvement log was too small for this path");
+            st = CSP_ERR_CAPACITY;
+        } else if (o[1] != ST_OK) {
+            set_error("csp_reconstruct_fast: inconsistent improvement record");
+            st = CSP_ERR_CUDA;
+        } else if (o[0] > cap) {
+            st = CSP_ERR_CAPACITY;
+        } else {
+            std::vector<long long> h((size_t)o[0]);
+            e = cudaMemcpy(h.data(), dpath, o[0] * 8, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                cudaFree(buf);
+                return cuda_fail(e, "csp_reconstruct_fast");
+            }
+            for (long long i = 0; i < o[0]; i++) path[i] = h[(size_t)(o[0] - 1 - i)];  // A end first
+        }
+    }
+    cudaFree(buf);
+    return st;
 }
 
 csp_status csp_get_labels(csp_lattice *L, int32_t *labels_host)

@@ -10,7 +10,8 @@ lexicographically smallest (F1, F2) walk.
 * 4096 x 4096, first 1500 cycles: trace rows, updates and launched flows against O1 run
   for the same number of cycles; at 512 x 512 the trace against the solve's own counts;
 * 48 x 48: the reconstructed path against the oracle's repeated application; 128 x 128:
-  the path's adjacency and sums.
+  the path's adjacency and sums; 4096 x 4096: the whole path from one recorded solve
+  against the oracle Dijkstra's predecessor chain.
 """
 import json
 import os
@@ -96,6 +97,19 @@ def test_full_size_answer_equals_lexicographic_dijkstra(csp, golden, full):
     assert lat.labels()[got.X] == inst.M - got.F2
 
 
+def test_full_size_path_equals_lexicographic_dijkstra(csp, golden, full):
+    """The whole 4096 x 4096 path from one recorded solve and a GPU backtrack (first
+    improvements only: the bound does not bind, so every path vertex is reached at its
+    first improvement) against the oracle Dijkstra's predecessor chain, which is the path
+    repeated application finds here (pinned in tests/test_oracle_pins.py)."""
+    inst, lat = full
+    F1, F2, X, xs, xd, want = oracle.lexmin(inst.extents, inst.f1, inst.f2, inst.A, inst.B, path=True)
+    got, r = lat.reconstruct_fast(inst.A, inst.B, inst.M, log_capacity=-1, time_limit_s=900)
+    assert r.answer() == (F1, X, xs, xd, F2)
+    assert got.tolist() == want
+    assert _path_sums(inst, want) == (F1, F2)
+
+
 def test_trace_counts_add_up_to_updates(csp, golden):
     inst = _instance(512, golden)
     lat = csp.Lattice(inst.extents, inst.f1, inst.f2)
@@ -115,7 +129,7 @@ def _path_sums(inst, path):
     t = w = 0
     for a, b in zip(path, path[1:]):
         lo, diff = min(a, b), abs(b - a)
-        k = st.index(diff)
+        k = max(i for i, sk in enumerate(st) if sk == diff and inst.extents[i] > 1)  # (extent-1 axes repeat a stride)
         c = synth.coords(np.array([lo]), inst.extents)[0]
         assert c[k] + 1 < inst.extents[k] and f1[k * V + lo] > 0, (a, b)
         t += f1[k * V + lo]

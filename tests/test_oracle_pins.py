@@ -233,3 +233,28 @@ def _scipy_lexmin(inst):
 def test_lexmin_equals_scipy_dijkstra_on_anticorrelated_lattices(side, seed):
     inst = synth.workload_anticorrelated(side, seed=seed)
     assert oracle.lexmin(inst.extents, inst.f1, inst.f2, inst.A, inst.B, full=True) == _scipy_lexmin(inst)
+
+
+@pytest.mark.parametrize("seed", range(2200, 2260))
+def test_lexmin_path_equals_repeated_application_where_the_bound_does_not_bind(seed):
+    """The Dijkstra predecessor chain is a second, independent route to the path that
+    repeated application of the cycle loop finds (Section 1) when the bound does not bind;
+    on tiny lattices its sums are also the brute-force optimum."""
+    inst = _tiny(seed)
+    F1, F2, X, xs, xd, path = oracle.lexmin(inst.extents, inst.f1, inst.f2, inst.A, inst.B, path=True)
+    if F1 < 0:
+        assert path is None
+        return
+    inst.M = F2 + 1 + seed % 5
+    want, _ = oracle.reconstruct(inst.extents, inst.f1, inst.f2, inst.A, inst.B, inst.M)
+    assert path == want
+    assert path[-1] == X and (len(path) == 1 or path[-2] == xs)
+    assert brute.brute_force(inst) == (F1, X, xs, xd, F2)
+
+
+def test_lexmin_path_on_anticorrelated_lattice_matches_repeated_application():
+    inst = synth.workload_anticorrelated(40, seed=7)
+    F1, F2, X, xs, xd, path = oracle.lexmin(inst.extents, inst.f1, inst.f2, inst.A, inst.B, path=True)
+    inst.M = (12 * F2) // 10
+    want, _ = oracle.reconstruct(inst.extents, inst.f1, inst.f2, inst.A, inst.B, inst.M)
+    assert path == want and path[0] == 0 and path[-1] == X

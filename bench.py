@@ -314,9 +314,63 @@ def run_ours(args):
         line["batched"] = bench_batched(csp, synth)
     if world == 1 and args.serve > 0:
         line["serving"] = bench_serving(csp, synth, args.serve)
+    if world == 1 and args.anticorrelated:
+        line["anticorrelated"] = bench_anticorrelated(csp, synth)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, ORACLE_SAMPLE_CYCLES)
     print(json.dumps(line), flush=True)
+
+
+def bench_anticorrelated(csp, synth):
+    """The 4096 x 4096 anti-correlated lattice (f1 geometric, f2 = 256 - f1, uint16, corner
+    to corner, M = floor(1.2 F2*)): time to solution of one solve and the whole path from
+    that solve (recorded first improvements + GPU backtrack), checked against the stored
+    answer of the oracle's lexicographic Dijkstra (tests/golden/anticorrelated_lexmin.json)."""
+    import torch
+    side = 4096
+    with open(os.path.join(ROOT, "tests", "golden", "anticorrelated_lexmin.json")) as f:
+        g = json.load(f)["sides"][str(side)]
+    inst = synth.workload_anticorrelated(side, M=g["M"])
+    lat = csp.Lattice(inst.extents, inst.f1, inst.f2)
+    lat.reserve(1 << 29)  # the flow pool peaks near 3.1e8 flows
+    s = torch.cuda.Stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for ev in (ev0, ev1):
+        ev.record(s)  # (an event has a handle once recorded)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    path, r = lat.reconstruct_fast(inst.A, inst.B, inst.M, log_capacity=-1, time_limit_s=900, stream=s,
+                                   ev_begin=ev0, ev_end=ev1)
+    wall = time.perf_counter() - t0
+    kern_s = ev0.elapsed_time(ev1) / 1e3
+    # the path's own sums, read from the weight arrays
+    st = synth.strides(inst.extents)
+    V = inst.V
+    f1 = inst.f1.reshape(-1).astype(np.int64)
+    f2 = inst.f2.reshape(-1).astype(np.int64)
+    a, b = path[:-1], path[1:]
+    lo = np.minimum(a, b)
+    k = np.where(np.abs(b - a) == st[0], 0, 1)
+    adjacent = bool(np.isin(np.abs(b - a), st).all())
+    sums = (int(f1[k * V + lo].sum()), int(f2[k * V + lo].sum())) if adjacent else (-1, -1)
+    out = {
+        "workload": "lattice2d_4096_anticorr_geom0.1_f2_256-f1_uint16_corner_to_corner_M1.2F2star",
+        "M": inst.M, "F1": r.F1, "F2": r.F2, "X": r.X, "x": [r.x_src, r.x_dir],
+        "answer_equals_oracle": r.answer() == (g["F1"], g["X"], g["x_src"], g["x_dir"], g["F2"]),
+        "cycles": r.cycles, "updates": r.updates, "launched": r.launched, "improved": r.improved,
+        "max_pool": r.max_pool,
+        "time_to_solution_s": kern_s,
+        "updates_per_s": r.updates / kern_s,
+        "path_vertices": int(len(path)),
+        "path_sums_equal_answer": sums == (r.F1, r.F2) and int(path[0]) == 0 and int(path[-1]) == r.X,
+        "solve_and_path_wall_s": wall,
+        "backtrack_and_copy_s": wall - kern_s,
+        "note": "cycle kernel timed with CUDA events (first improvements recorded for the backtrack); "
+                "the path needs one solve, repeated application would need one per path vertex",
+    }
+    lat.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_batched(csp, synth):
@@ -348,7 +402,7 @@ def bench_batched(csp, synth):
     devB = [torch.from_numpy(i.B).cuda() for i in insts]
     rec = torch.zeros((len(insts), 16), dtype=torch.int64, device="cuda")
     for L, i in zip(lats, insts):
-        L.reserve(max(1 << 16, 6 * i.V))
+        L.reserve()  # the default pool (with room for part-filled chunks); plain solves cannot grow it
     torch.cuda.synchronize()
 
     def plain():
@@ -358,6 +412,7 @@ def bench_batched(csp, synth):
     ms_p = timed(plain)
     r = rec.cpu().numpy()
     agree = sum(1 for k in range(len(insts)) if r[k, 0] == 0 and tuple(int(x) for x in r[k, 1:6]) == res[k].answer())
+    plain_ok = int((r[:, 0] == 0).sum())
     upd = sum(x.updates for x in res)
     b.close()
     for L in lats:
@@ -368,7 +423,8 @@ def bench_batched(csp, synth):
             "instances_per_s": n / (ms_b / 1e3), "plain_instances_per_s": n / (ms_p / 1e3),
             "speedup_vs_plain": ms_p / ms_b, "batched_ms": ms_b, "plain_ms": ms_p,
             "updates_per_s": upd / (ms_b / 1e3), "updates": upd,
-            "statuses_ok": sum(1 for x in res if x.status == 0), "agree_with_plain": agree,
+            "statuses_ok": sum(1 for x in res if x.status == 0), "plain_statuses_ok": plain_ok,
+            "agree_with_plain": agree,
             "schedule": {"ctas": sched["ctas"], "group_sizes": {str(g): int((sched["group"] == g).sum())
                                                                 for g in sorted(set(sched["group"].tolist()))},
                          "planned_makespan_ms": model["makespan_us"] / 1e3,
@@ -440,6 +496,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=1, help="also measure 512 batched instances vs one launch each (N=1)")
+    ap.add_argument("--anticorrelated", type=int, default=1,
+                    help="also time the 4096^2 anti-correlated solve and its path (N=1; ~1.5 min)")
     ap.add_argument("--serve", type=int, default=2000,
                     help="queries per rate for the serving comparison on the 48^4 lattice (0 = skip; N=1 only)")
     args = ap.parse_args()

@@ -232,15 +232,16 @@ class Lattice:
         return out[: n.value].copy() if n.value else None
 
     def reconstruct_fast(self, A, B, M: int, *, log_capacity: int = 0, cap: int = 1 << 20, max_cycles: int = 0,
-                         ctas: int = 0, time_limit_s: int = 0, stream=None):
+                         ctas: int = 0, time_limit_s: int = 0, stream=None, ev_begin=None, ev_end=None):
         """``csp_reconstruct_fast``: one recorded solve and a GPU backtrack.
 
         Returns ``(path, result)``; ``path`` is None if infeasible.  ``log_capacity`` < 0 keeps
         first improvements only (enough when the bound does not bind along the path).
+        ``ev_begin``/``ev_end``: optional CUDA events recorded around the cycle kernel.
         """
         A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
         B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
-        opt = options(max_cycles, 0, ctas, stream, time_limit_s=time_limit_s)
+        opt = options(max_cycles, 0, ctas, stream, ev_begin, ev_end, time_limit_s)
         res = CspResult()
         out = np.zeros(cap, np.int64)
         n = ctypes.c_int64(0)

@@ -84,6 +84,15 @@ __device__ __forceinline__ Params<W> batch_params(const BatchInstance &I, unsign
     return P;
 }
 
+// One instance on its group, out of line: the four dimensions' solves get registers of
+// their own instead of sharing (and spilling) one inlined body.
+template <int D, typename W>
+__device__ __noinline__ void batch_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t (&parity)[NSTAGE],
+                                         unsigned long long &epoch)
+{
+    run_solve<D, W, false>(P, g, sm, parity, epoch);
+}
+
 template <typename W>
 __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM)
     k_batch(const BatchInstance *insts, const int *list_start, const BatchWork *work, unsigned long long budget_ns)
@@ -93,18 +102,24 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM)
     init_stage_barriers(sm);
     uint32_t parity[NSTAGE] = {};
     const int first = list_start[blockIdx.x], last = list_start[blockIdx.x + 1];
+    // the instance's parameters live in shared memory (read like kernel arguments), not in
+    // registers
+    __shared__ Params<W> s_P;
     for (int i = first; i < last; i++) {
         const BatchWork w = work[i];
         const BatchInstance &I = insts[w.inst];
         const Group g{(uint32_t)w.rank, (uint32_t)w.size};
-        const Params<W> P = batch_params<W>(I, budget_ns);
+        __syncthreads();  // the previous instance is done with s_P
+        if (threadIdx.x == 0) s_P = batch_params<W>(I, budget_ns);
+        __syncthreads();
+        const Params<W> &P = s_P;
         unsigned long long epoch = 0;
         group_setup<W>(P, g, I.A, I.nA, I.B, I.nB, epoch);  // a failed barrier also fails the solve's first one
         switch (I.d) {
-        case 1: run_solve<1, W, false>(P, g, sm, parity, epoch); break;
-        case 2: run_solve<2, W, false>(P, g, sm, parity, epoch); break;
-        case 3: run_solve<3, W, false>(P, g, sm, parity, epoch); break;
-        default: run_solve<4, W, false>(P, g, sm, parity, epoch); break;
+        case 1: batch_solve<1, W>(P, g, sm, parity, epoch); break;
+        case 2: batch_solve<2, W>(P, g, sm, parity, epoch); break;
+        case 3: batch_solve<3, W>(P, g, sm, parity, epoch); break;
+        default: batch_solve<4, W>(P, g, sm, parity, epoch); break;
         }
         __syncthreads();
     }

@@ -567,45 +567,25 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
     __syncthreads();
     bool ok = true;
     uint32_t k = 0;
-    // software pipeline per warp: the label gathers of the next tile are in flight while
-    // the current tile is classified and written out
-    uint32_t eN[IPT], nfN = 0;
-    int32_t LN[IPT];
-    if (g.rank < n_tiles) {
-        ok = wait_stage_warp(sm, 0, parity[0]);
-        parity[0] ^= 1u;
-        nfN = sm.stage_fill[0];
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
-            eN[i] = j < nfN ? sm.in_ed[0][j] : 0u;
-            LN[i] = j < nfN ? __ldcg(P.label + (eN[i] >> 3)) : INT_MAX;
-        }
-    }
     int s = 0;  // stage of the current tile (k mod NSTAGE)
-    for (uint32_t tile = g.rank; ok && tile < n_tiles; tile += G, k++, s = s + 1 == NSTAGE ? 0 : s + 1) {
-        const int sn = s + 1 == NSTAGE ? 0 : s + 1;  // stage of the next tile
-        const uint32_t nfill = nfN;
+    for (uint32_t tile = g.rank; tile < n_tiles; tile += G, k++, s = s + 1 == NSTAGE ? 0 : s + 1) {
+        if (!wait_stage_warp(sm, s, parity[s])) {
+            ok = false;
+            break;
+        }
+        parity[s] ^= 1u;
+        const uint32_t nfill = sm.stage_fill[s];
         uint32_t e[IPT];
         int32_t L[IPT];
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
-            e[i] = eN[i];
-            L[i] = LN[i];
+            const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
+            e[i] = j < nfill ? sm.in_ed[s][j] : 0u;
         }
-        if (tile + G < n_tiles) {  // next tile: wait for its stage, start its gathers
-            if (!wait_stage_warp(sm, sn, parity[sn])) {
-                ok = false;
-                break;
-            }
-            parity[sn] ^= 1u;
-            nfN = sm.stage_fill[sn];
 #pragma unroll
-            for (int i = 0; i < IPT; i++) {
-                const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
-                eN[i] = j < nfN ? sm.in_ed[sn][j] : 0u;
-                LN[i] = j < nfN ? __ldcg(P.label + (eN[i] >> 3)) : INT_MAX;
-            }
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
+            L[i] = j < nfill ? __ldcg(P.label + (e[i] >> 3)) : INT_MAX;
         }
         uint32_t bk[IPT], ba[IPT];
         uint32_t nk = 0, na = 0;

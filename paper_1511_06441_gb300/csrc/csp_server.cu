@@ -93,7 +93,12 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
     const int gid = blockIdx.x / S.group_ctas;
     const Group g{(uint32_t)(blockIdx.x % S.group_ctas), (uint32_t)S.group_ctas};
     const GroupSlot &slot = S.slots[gid];
-    Params<W> P{};
+    // the slot's parameters live in shared memory (read like kernel arguments), not in registers
+    __shared__ Params<W> s_P;
+    if (threadIdx.x == 0) s_P = Params<W>{};
+    __syncthreads();
+    Params<W> &P = s_P;
+    if (threadIdx.x == 0) {
     P.rec = S.rec;
     P.V = S.V;
     for (int k = 0; k < 4; k++) P.stride[k] = S.stride[k];
@@ -115,6 +120,8 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
     P.touched_n = slot.touched_n;
     P.budget_ns = 120ull * 1000000000ull;
     P.barrier_ns = S.session_ns;  // an idle group waits for work at its barrier
+    }
+    __syncthreads();
     unsigned long long epoch = 0;
     const unsigned long long t_begin = globaltimer_ns();
     __shared__ long long s_pos;
@@ -154,8 +161,11 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
         }
         __syncthreads();
         const QueryDesc &q = s_q;
-        P.M = q.M;
-        P.max_cycles = q.max_cycles;
+        if (threadIdx.x == 0) {
+            P.M = q.M;
+            P.max_cycles = q.max_cycles;
+        }
+        __syncthreads();
         const TargetSet T{nullptr, q.nB > 0 ? q.B : nullptr, q.nB, q.nB > 0 ? -1 : q.axis, q.coord};
         // the slot's labels, offers and B bitmap are all zero here (zeroed at creation and
         // undone after every query), so the set-up touches only A and B

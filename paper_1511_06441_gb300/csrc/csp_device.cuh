@@ -594,13 +594,17 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
             const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
             const int32_t q = j < nfill ? sm.in_qa[s][j] : 0;
             bool keep = false, arr = false;
-            if (q > L[i]) {  // live (padding has q = 0 <= INT_MAX)
+            const bool live = q > L[i];  // (padding has q = 0 <= INT_MAX)
+            if (TRACE) {
+                // set the source's bit once per warp and source: a source's flows were written
+                // to consecutive slots, so they usually meet in one warp step
+                const uint32_t src = (uint32_t)((int)(e[i] >> 3) + dir_offset<D>(P.stride, e[i] & 7u));
+                const uint32_t m = __match_any_sync(0xffffffffu, live ? src : 0xffffffffu - (uint32_t)lane);
+                if (live && __ffs(m) - 1 == lane) atomicOr(P.srcbits + (src >> 5), 1u << (src & 31));
+            }
+            if (live) {
                 st.live++;
                 const uint32_t dst = e[i] >> 3;
-                if (TRACE) {
-                    const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(P.stride, e[i] & 7u));
-                    atomicOr(P.srcbits + (src >> 5), 1u << (src & 31));
-                }
                 const int32_t t = sm.in_ta[s][j];
                 if (t == Tg) {
                     const unsigned long long key =
@@ -714,36 +718,36 @@ __device__ __forceinline__ uint32_t launch_mask(const EdgeRecord<W, D> &r, int L
 }
 
 // Warp-collective: appends the flows of mask (per lane, one source vertex v with label Lv)
-// to the output pool with one shared-memory claim per warp.  Flows are laid out direction
-// by direction (a ballot per direction), so that every store instruction of the warp
-// writes one contiguous run of slots.
+// to the output pool with one shared-memory claim per warp.  Each lane writes its flows to
+// consecutive slots (so the flows of one source stay together for the trace count of
+// later sweeps).
 template <typename W, int D>
 __device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters *C, Smem &sm, uint32_t v, int Lv,
                                            const EdgeRecord<W, D> &r, uint32_t mask, int Time, LocalStats &st)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t bd[2 * D], total = 0;
+    const uint32_t nk = __popc(mask);
+    uint32_t incl = nk;
 #pragma unroll
-    for (int dir = 0; dir < 2 * D; dir++) {
-        bd[dir] = __ballot_sync(0xffffffffu, (mask >> dir) & 1u);
-        total += __popc(bd[dir]);
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     if (total == 0) return;
     const Span sp = claim_slots(sm, C, P.ctl, P.fill[ob], total, P.pool_cap / (uint32_t)TILE);
     st.written += lane == 0 ? total : 0u;
-    uint32_t p = sp.f0;
+    uint32_t p = sp.f0 + incl - nk;
 #pragma unroll
-    for (int dir = 0; dir < 2 * D; dir++) {
-        if ((bd[dir] >> lane) & 1u) {
+    for (int dir = 0; dir < 2 * D; dir++)
+        if (mask & (1u << dir)) {
             const uint32_t w = v + dir_offset<D>(P.stride, dir);
             const int t = Time + r.f1(dir);
-            put_flow(P, ob, C, sp, p + __popc(bd[dir] & lt), (w << 3) | (uint32_t)(dir ^ 1), Lv - r.f2(dir), t);
+            put_flow(P, ob, C, sp, p, (w << 3) | (uint32_t)(dir ^ 1), Lv - r.f2(dir), t);
+            p++;
             st.min_ta = min(st.min_ta, t);
             st.launched++;
         }
-        p += __popc(bd[dir]);
-    }
 }
 
 // One thread per arrival candidate of this CTA's region.  The candidate whose code equals

@@ -67,6 +67,7 @@ struct Counters {
 };
 
 constexpr int NRELEASE = 32;  // copies of the barrier's release word, one per 128-byte line
+constexpr int MAX_GROUP = 1024;  // most CTAs one group may have
 
 struct ReleaseWord {
     alignas(128) unsigned long long epoch;
@@ -157,8 +158,10 @@ struct Smem {
     int fail;                      // a bounded wait gave up
 };
 
-constexpr uint32_t NO_CHUNK = 0xffffffffu;   // no chunk allocated
-constexpr uint32_t OVF_CHUNK = 0xfffffffeu;  // allocation beyond the pool: writes dropped, overflow set
+constexpr uint32_t NO_CHUNK = 0xffffffffu;    // no chunk allocated
+constexpr uint32_t OVF_CHUNK = 0xfffffffeu;   // allocation beyond the pool: writes dropped, overflow set
+constexpr uint32_t LAZY_CHUNK = 0xfffffffdu;  // cursor not opened yet: the first claim allocates
+constexpr uint32_t FIRST_SPECIAL = 0xfffffff0u;  // chunk ids from here on name no chunk
 
 // The CTAs that cooperate on one solve: the whole grid for a single solve, a slice of
 // it in batched mode.  rank = index of this CTA in the group.
@@ -402,19 +405,12 @@ __device__ __forceinline__ unsigned long long pack_cursor(uint32_t chunk, uint32
     return ((unsigned long long)chunk << 32) | fill;
 }
 
-// Thread 0, at the start of a pass of a CTA that will write flows: allocates the chunk to
-// fill and the one after it with one atomic.  (A CTA with nothing to write allocates
-// nothing; its cursor holds NO_CHUNK.)
-__device__ __forceinline__ void cursor_open(Smem &sm, Counters *C, uint32_t n_chunks, bool will_write)
+// Thread 0, at the start of a pass: the CTA's cursor opens on its first claim (a CTA that
+// writes nothing allocates nothing).
+__device__ __forceinline__ void cursor_open(Smem &sm)
 {
-    uint32_t c0 = NO_CHUNK, c1 = NO_CHUNK;
-    if (will_write) {
-        const uint32_t c = atomicAdd(&C->chunks, 2u);
-        c0 = c < n_chunks ? c : OVF_CHUNK;
-        c1 = c + 1 < n_chunks ? c + 1 : OVF_CHUNK;
-    }
-    sm.cursor = pack_cursor(c0, 0);
-    sm.next_chunk = c1;
+    sm.cursor = pack_cursor(LAZY_CHUNK, 0);
+    sm.next_chunk = NO_CHUNK;
 }
 
 // Slots [f0, f0 + n) of the CTA's output, the part from TILE on in chunk c1.
@@ -440,7 +436,21 @@ __device__ __forceinline__ Span claim_slots(Smem &sm, Counters *C, Control *ctl,
         for (uint32_t tries = 0; tries < 4096u && !done; tries++) {
             const unsigned long long old = atomicAdd(&sm.cursor, (unsigned long long)n);
             const uint32_t id = hi32(old), f = lo32(old);
-            if (f + n < (uint32_t)TILE) {  // inside the current chunk
+            if (id == LAZY_CHUNK) {
+                if (f == 0) {  // the first claim of the pass: allocate this chunk and the next
+                    const uint32_t c = atomicAdd(&C->chunks, 2u);
+                    c0 = c < n_chunks ? c : OVF_CHUNK;
+                    *vnext = c + 1 < n_chunks ? c + 1 : OVF_CHUNK;
+                    __threadfence_block();
+                    atomicExch(&sm.cursor, pack_cursor(c0, n));
+                    f0 = 0;
+                    done = true;
+                } else {  // wait for the first claim to open the cursor
+                    uint32_t spin = 0;
+                    for (; spin < (1u << 22) && hi32(*vcur) == LAZY_CHUNK; spin++) __nanosleep(32);
+                    if (spin >= (1u << 22)) break;
+                }
+            } else if (f + n < (uint32_t)TILE) {  // inside the current chunk
                 c0 = id;
                 f0 = f;
                 done = true;
@@ -458,7 +468,7 @@ __device__ __forceinline__ Span claim_slots(Smem &sm, Counters *C, Control *ctl,
                 *vnext = NO_CHUNK;
                 __threadfence_block();
                 atomicExch(&sm.cursor, pack_cursor(nx, f + n - (uint32_t)TILE));
-                if (id < OVF_CHUNK) fill_out[id] = (uint32_t)TILE;
+                if (id < FIRST_SPECIAL) fill_out[id] = (uint32_t)TILE;
                 c0 = id;
                 f0 = f;
                 c1 = nx;
@@ -491,7 +501,7 @@ __device__ __forceinline__ bool span_slot(const Span &sp, uint32_t p, uint32_t &
 {
     const uint32_t c = p < (uint32_t)TILE ? sp.c0 : sp.c1;
     idx = c * (uint32_t)TILE + (p < (uint32_t)TILE ? p : p - (uint32_t)TILE);
-    return c < OVF_CHUNK;
+    return c < FIRST_SPECIAL;
 }
 
 // Thread 0, after the pass's last write (a __syncthreads in between): records how full the
@@ -502,8 +512,8 @@ __device__ __forceinline__ void cursor_close(const Params<W> &P, Smem &sm, int o
     if (threadIdx.x == 0) {
         const unsigned long long cur = sm.cursor;
         const uint32_t id = hi32(cur), nx = sm.next_chunk;
-        if (id < OVF_CHUNK) P.fill[ob][id] = min(lo32(cur), (uint32_t)TILE);
-        if (nx < OVF_CHUNK) P.fill[ob][nx] = 0u;
+        if (id < FIRST_SPECIAL) P.fill[ob][id] = min(lo32(cur), (uint32_t)TILE);
+        if (nx < FIRST_SPECIAL) P.fill[ob][nx] = 0u;
         // (a chunk past the pool was handed out but not written to: put_flow flags a lost flow)
         sm.cursor = pack_cursor(NO_CHUNK, 0);
         sm.next_chunk = NO_CHUNK;
@@ -547,15 +557,18 @@ __device__ __forceinline__ void put_flow(const Params<W> &P, int ob, Counters *C
 #endif
 
 template <int D, typename W, bool TRACE>
-__device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_tiles, int Tg, Counters *C,
-                                       LocalStats &st, Smem &sm, uint32_t (&parity)[NSTAGE], uint32_t cand_base,
-                                       uint32_t cand_cap)
+__device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_tiles, int Tg,
+                                       Counters *C, LocalStats &st, Smem &sm, uint32_t (&parity)[NSTAGE],
+                                       uint32_t cand_base, uint32_t cand_cap)
 {
     const int ob = ib ^ 1;
-    const uint32_t G = g.size;
     const uint32_t n_chunks = P.pool_cap / (uint32_t)TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
+    // Tiles are dealt round-robin: tile rank + k G goes to stage k mod NSTAGE.  (Claiming
+    // tiles from a counter balanced the CTAs but its returning atomic on the refill path cost
+    // more than the balance gained: 6.1 vs 5.2 s on a 2048^2 lattice.)
+    const uint32_t G = g.size;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; s++) sm.read_cnt[s] = 0;
         sm.n_cand = 0;
@@ -649,7 +662,7 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
                 p += __popc(bk[i]);
             }
         }
-        // this warp is done with stage s; the last warp refills it with tile + NSTAGE * G
+        // this warp is done with stage s; the last warp refills it with tile + NSTAGE G
         __threadfence_block();
         __syncwarp();
         if (lane == 0) {
@@ -658,6 +671,7 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
                 __threadfence_block();
                 sm.read_cnt[s] = 0;
                 if (tile + NSTAGE * G < n_tiles) {
+                    fence_proxy_async_global();  // (this lane's view of the pool written last pass)
                     fence_proxy_async_smem();
                     issue_tile(P, sm, s, ib, tile + NSTAGE * G);
                 }
@@ -665,11 +679,9 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
         }
     }
     bool pending[NSTAGE];
-    // copies possibly issued but never waited for (only after a give-up): the next NSTAGE tiles
-    for (int q = 0; q < NSTAGE; q++) pending[q] = false;
+    // stages that may still receive a copy (only after a give-up): the next NSTAGE tiles
+    for (int q = 0; q < NSTAGE; q++) pending[(s + q) % NSTAGE] = !ok && g.rank + (k + q) * G < n_tiles;
     if (!ok) {
-        for (int q = 0; q < NSTAGE; q++)
-            if (g.rank + (k + q) * G < n_tiles) pending[(s + q) % NSTAGE] = true;
         sm.fail = 1;
         atomicExch(&P.ctl->err, 1);
     }
@@ -759,7 +771,7 @@ __device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters 
 // together.  Warps work independently.  With TRACE, also counts (and clears) the source
 // bitmap filled by the sweep.
 template <int D, typename W, bool TRACE>
-__device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int ob, uint32_t cand_base, uint32_t n_cand,
+__device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int ob, uint32_t cand_cta, bool with_cands,
                                         int Time, Counters *C, LocalStats &st, Smem &sm)
 {
     const uint32_t V = (uint32_t)P.V;
@@ -773,6 +785,8 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
             }
         }
     }
+    if (!with_cands) return;
+    const uint32_t n_cand = min(sm.n_cand, cand_cta), cand_base = g.rank * cand_cta;
     const uint32_t wbase = (threadIdx.x >> 5) * 32u;
     for (uint32_t base = wbase; base < n_cand; base += TPB) {
         const uint32_t j = base + (threadIdx.x & 31);
@@ -957,7 +971,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
         LocalStats st{0, 0, 0, 0, 0, 0, INT_MAX};
         const uint32_t n_src = min(hi32(read_shared_u64(&ctl->cnt[0].out_cand)), P.cand_cap);
         // (the seed adds the flows it writes to the low half of out_cand; the high half keeps n_src)
-        if (threadIdx.x == 0) cursor_open(sm, &ctl->cnt[0], n_chunks, g.rank * TPB < n_src);
+        if (threadIdx.x == 0) cursor_open(sm);
         __syncthreads();
         seed<D, W>(P, g, n_src, &ctl->cnt[0], st, sm);
         __syncthreads();
@@ -981,7 +995,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             const int ib = (int)((pass - 1) & 1), ob = ib ^ 1;
             Counters *C = &ctl->cnt[ob];
             LocalStats sa{0, 0, 0, 0, 0, 0, INT_MAX};
-            if (threadIdx.x == 0) cursor_open(sm, C, n_chunks, g.rank < n_tiles);
+            if (threadIdx.x == 0) cursor_open(sm);
             if (!sweep<D, W, TRACE>(P, g, ib, n_tiles, Tg, C, sa, sm, parity, cand_base, cand_cta)) {
                 status = ST_BARRIER;
                 goto finish;
@@ -995,7 +1009,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             }
             if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
             LocalStats sb{0, 0, 0, 0, 0, 0, INT_MAX};
-            launch<D, W, TRACE>(P, g, ob, cand_base, min(sm.n_cand, cand_cta), Tg, C, sb, sm);
+            launch<D, W, TRACE>(P, g, ob, cand_cta, true, Tg, C, sb, sm);
             __syncthreads();
             cursor_close(P, sm, ob);
             flush_stats(sb, C);
@@ -1024,7 +1038,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                         // the terminal cycle's row: count the flows still alive after it
                         LocalStats sc{0, 0, 0, 0, 0, 0, INT_MAX};
                         const uint32_t nt = min(c.chunks, n_chunks);
-                        if (threadIdx.x == 0) cursor_open(sm, &ctl->cnt[ib], n_chunks, g.rank < nt);
+                        if (threadIdx.x == 0) cursor_open(sm);
                         if (!sweep<D, W, TRACE>(P, g, ob, nt, -1, &ctl->cnt[ib], sc, sm, parity, cand_base,
                                                 cand_cta)) {
                             status = ST_BARRIER;
@@ -1033,7 +1047,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                         flush_stats(sc, &ctl->cnt[ib]);
                         if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
                         LocalStats sd{0, 0, 0, 0, 0, 0, INT_MAX};
-                        launch<D, W, TRACE>(P, g, ib, cand_base, 0, Time, &ctl->cnt[ib], sd, sm);  // count sources
+                        launch<D, W, TRACE>(P, g, ib, cand_cta, false, Time, &ctl->cnt[ib], sd, sm);  // count sources
                         __syncthreads();
                         cursor_close(P, sm, ib);
                         flush_stats(sd, &ctl->cnt[ib]);

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
 
@@ -69,7 +70,7 @@ struct ReconLog {
 
 // Largest group of CTAs one solve may use on a device: the candidate list of a workspace
 // is sized for it (one region per CTA).
-inline int max_group_ctas(int device) { return 4 * num_sms(device); }
+inline int max_group_ctas(int device) { return std::min(4 * num_sms(device), csp::MAX_GROUP); }
 
 // Pool slots a pass may leave unused: each CTA of a group holds one partly filled chunk
 // and one chunk allocated ahead.

@@ -47,6 +47,21 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_rate(local_s: float, units_per_rank: float, world: int, device=None):
+    """Whole-job (time, rate) over replicas: every rank processed ``units_per_rank`` units in
+    ``local_s`` seconds; the job's time is the slowest rank's (max over ranks) and the units
+    of all ranks add up.  With ``world`` > 1 the process group must be initialised (NCCL on
+    GPUs; the tests use gloo on CPU)."""
+    total_s = float(local_s)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return total_s, world * units_per_rank / total_s
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -223,13 +238,8 @@ def run_ours(args):
     assert (out[:, 0] == 0).all() and (out[:, 1:12] == ref[:, 1:12]).all(), "results changed between steps"
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     kern_ms = [[a.elapsed_time(b) for a, b in row] for row in kern_ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
     upd_per_step = int(out[:, 7].sum())
-    value = world * K * upd_per_step / total_s
+    total_s, value = replica_rate(sum(step_ms) / 1e3, K * upd_per_step, world, dev)
 
     # roofline of the cycle kernel (the only kernel that scales with the work)
     d = 3
@@ -272,14 +282,10 @@ def run_ours(args):
                 r = lat2.solve(hA, hB, M, trace=args.trace, trace_cap=trace_cap)
                 e2e_upd += r.updates
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
+        dt, e2e_rate = replica_rate(time.perf_counter() - t0, e2e_upd, world, dev)
         h2d = inst.f1.nbytes + inst.f2.nbytes + nM * (hA.nbytes + hB.nbytes)
         d2h = nM * (16 * 8 + (3 * 8 * trace_cap if args.trace else 0))
-        e2e = {"value": world * e2e_upd / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
                "ms_per_step": 1e3 * dt / args.e2e_steps}
         lat2.close()

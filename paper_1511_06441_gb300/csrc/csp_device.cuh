@@ -183,10 +183,6 @@ __device__ __forceinline__ int dir_offset(const int (&stride)[4], unsigned r)
     return (r & 1) ? -s : s;
 }
 
-__device__ __forceinline__ bool in_set(const uint32_t *bits, uint32_t v)
-{
-    return (__ldcg(bits + (v >> 5)) >> (v & 31)) & 1u;
-}
 
 // x code of a flow arriving at dst from direction r (r = direction from dst back to the
 // source): ~(src * 8 + dir), dir = r ^ 1 the direction from the source to dst.
@@ -802,6 +798,7 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
             r = load_record<W, D>(P.rec, v);
             int Lw[2 * D];
             neighbour_labels<D>(P.offer, P.stride, V, v, Lw);
+            const uint32_t bw = __ldcg(P.isB + (v >> 5));  // (issued with the other loads)
             if (lo32(ov) == code) {  // the winning arrival at v
                 won = true;
                 Lv = (int)hi32(ov);
@@ -814,7 +811,7 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
                 }
                 P.label[v] = Lv;
                 st.improved++;
-                if (in_set(P.isB, v))
+                if ((bw >> (v & 31)) & 1u)
                     atomicMax(&C->xkey, ((unsigned long long)(uint32_t)Lv << 32) | (0xffffffffu - v));
                 mask = launch_mask<W, D>(r, Lv, Lw);
             }

@@ -1,7 +1,7 @@
 // Device-side building blocks of the water-flow cycle (arXiv 1511.06441, Algorithm 1):
 // the flow-pool sweep (Steps 1-3 and 7-9), the launch phase (Steps 2, 4, 5 and the
-// label part of Step 8), block-level compaction, a TMA (bulk-copy) tile pipeline and a
-// spin-limited grid barrier.
+// label part of Step 8), warp-level compaction into per-CTA pool chunks, a TMA (bulk-copy)
+// tile pipeline and a spin-limited grid barrier.
 //
 // Data layout in HBM (one solve):
 //   label[V]  int32   committed labels, frozen while the pool is swept

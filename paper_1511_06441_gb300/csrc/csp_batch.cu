@@ -63,7 +63,7 @@ __device__ __forceinline__ Params<W> batch_params(const BatchInstance &I, unsign
     P.label = I.label;
     P.offer = I.offer;
     P.isB = I.isB;
-    P.srcbits = nullptr;
+    P.src_stamp = nullptr;
     P.cand = I.cand;
     P.cand_cap = I.cand_cap;
     for (int b = 0; b < 2; b++) {

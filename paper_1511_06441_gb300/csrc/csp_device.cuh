@@ -8,7 +8,7 @@
 //   offer[V]  uint64  running max of (quality << 32 | ~(src*8 + dir)) over all arrivals;
 //                     its high half equals label[] at every cycle boundary
 //   isB[V/32] uint32  bitmap of B
-//   srcbits   uint32  bitmap of the sources of live flows (trace mode), cleared each pass
+//   src_stamp uint32  per vertex: the last pass in which it sourced a live flow (trace mode)
 //   cand[]    uint32  arrivals of the current cycle (flow word ed of each arriving flow),
 //                     one region of cand_cap / G entries per CTA of the group
 //   pool[2]   SoA     ed = dst << 3 | direction back to the source (uint32),
@@ -112,7 +112,7 @@ struct Params {
     int32_t *label;
     unsigned long long *offer;
     const uint32_t *isB;
-    uint32_t *srcbits;             // trace mode: sources of live flows, (V + 31) / 32 words
+    uint32_t *src_stamp;           // trace mode: [V rounded up to 4] last pass each vertex sourced a live flow
     uint32_t *cand;                // arrivals of the current cycle (the sources of A at the seed)
     unsigned int cand_cap;
     uint32_t *ed[2];
@@ -545,7 +545,7 @@ __device__ __forceinline__ void put_flow(const Params<W> &P, int ob, Counters *C
 // loop): the last warp to finish reading a stage starts the copy of the tile after next
 // into it, and each warp compacts its survivors and arrivals with ballots and claims
 // output room with one shared-memory atomic.  With TRACE, live flows set their source's
-// bit in srcbits (counted by the launch phase).
+// stamp (src_stamp = the pass number; counted by the launch phase).
 // The CTA's output cursor must be open.  Returns false (uniformly across the CTA) if a
 // bounded wait gave up (ctl->err set).
 #ifndef CSP_PHASE_INLINE
@@ -554,7 +554,7 @@ __device__ __forceinline__ void put_flow(const Params<W> &P, int ob, Counters *C
 
 template <int D, typename W, bool TRACE>
 __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_tiles, int Tg,
-                                       Counters *C, LocalStats &st, Smem &sm, uint32_t (&parity)[NSTAGE],
+                                       uint32_t stamp, Counters *C, LocalStats &st, Smem &sm, uint32_t (&parity)[NSTAGE],
                                        uint32_t cand_base, uint32_t cand_cap)
 {
     const int ob = ib ^ 1;
@@ -604,12 +604,9 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
             const int32_t q = j < nfill ? sm.in_qa[s][j] : 0;
             bool keep = false, arr = false;
             const bool live = q > L[i];  // (padding has q = 0 <= INT_MAX)
-            if (TRACE) {
-                // set the source's bit once per warp and source: a source's flows were written
-                // to consecutive slots, so they usually meet in one warp step
+            if (TRACE && live) {  // the source is active in this pass (a plain store: every writer agrees)
                 const uint32_t src = (uint32_t)((int)(e[i] >> 3) + dir_offset<D>(P.stride, e[i] & 7u));
-                const uint32_t m = __match_any_sync(0xffffffffu, live ? src : 0xffffffffu - (uint32_t)lane);
-                if (live && __ffs(m) - 1 == lane) atomicOr(P.srcbits + (src >> 5), 1u << (src & 31));
+                P.src_stamp[src] = stamp;
             }
             if (live) {
                 st.live++;
@@ -764,21 +761,19 @@ __device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters 
 // a flow on every edge (v, w) with Label(v) - f2 > Label(w) under the labels at the end of
 // this cycle (Steps 4-5; a flow on an edge that already carries water is the paper's
 // phantom).  Its loads (offer[v], the edge record, the 2d neighbour labels) are issued
-// together.  Warps work independently.  With TRACE, also counts (and clears) the source
-// bitmap filled by the sweep.
+// together.  Warps work independently.  With TRACE, also counts the vertices the sweep
+// stamped with this pass.
 template <int D, typename W, bool TRACE>
 __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int ob, uint32_t cand_cta, bool with_cands,
-                                        int Time, Counters *C, LocalStats &st, Smem &sm)
+                                        int Time, uint32_t stamp, Counters *C, LocalStats &st, Smem &sm)
 {
     const uint32_t V = (uint32_t)P.V;
-    if (TRACE) {
-        const uint32_t words = (V + 31) / 32;
-        for (uint32_t w = g.rank * TPB + threadIdx.x; w < words; w += g.size * TPB) {
-            const uint32_t b = __ldcg(P.srcbits + w);
-            if (b) {
-                st.active += __popc(b);
-                P.srcbits[w] = 0u;
-            }
+    if (TRACE) {  // active vertices: stamped by this pass's sweep (16-byte loads, 4 vertices each)
+        const uint4 *st4 = reinterpret_cast<const uint4 *>(P.src_stamp);
+        const uint32_t n4 = (V + 3) / 4;
+        for (uint32_t i = g.rank * TPB + threadIdx.x; i < n4; i += g.size * TPB) {
+            const uint4 x = __ldcg(st4 + i);
+            st.active += (x.x == stamp) + (x.y == stamp) + (x.z == stamp) + (x.w == stamp);
         }
     }
     if (!with_cands) return;
@@ -993,7 +988,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             Counters *C = &ctl->cnt[ob];
             LocalStats sa{0, 0, 0, 0, 0, 0, INT_MAX};
             if (threadIdx.x == 0) cursor_open(sm);
-            if (!sweep<D, W, TRACE>(P, g, ib, n_tiles, Tg, C, sa, sm, parity, cand_base, cand_cta)) {
+            if (!sweep<D, W, TRACE>(P, g, ib, n_tiles, Tg, (uint32_t)pass, C, sa, sm, parity, cand_base, cand_cta)) {
                 status = ST_BARRIER;
                 goto finish;
             }
@@ -1006,7 +1001,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             }
             if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
             LocalStats sb{0, 0, 0, 0, 0, 0, INT_MAX};
-            launch<D, W, TRACE>(P, g, ob, cand_cta, true, Tg, C, sb, sm);
+            launch<D, W, TRACE>(P, g, ob, cand_cta, true, Tg, (uint32_t)pass, C, sb, sm);
             __syncthreads();
             cursor_close(P, sm, ob);
             flush_stats(sb, C);
@@ -1036,7 +1031,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                         LocalStats sc{0, 0, 0, 0, 0, 0, INT_MAX};
                         const uint32_t nt = min(c.chunks, n_chunks);
                         if (threadIdx.x == 0) cursor_open(sm);
-                        if (!sweep<D, W, TRACE>(P, g, ob, nt, -1, &ctl->cnt[ib], sc, sm, parity, cand_base,
+                        if (!sweep<D, W, TRACE>(P, g, ob, nt, -1, (uint32_t)pass + 1u, &ctl->cnt[ib], sc, sm, parity, cand_base,
                                                 cand_cta)) {
                             status = ST_BARRIER;
                             goto finish;
@@ -1044,7 +1039,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                         flush_stats(sc, &ctl->cnt[ib]);
                         if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
                         LocalStats sd{0, 0, 0, 0, 0, 0, INT_MAX};
-                        launch<D, W, TRACE>(P, g, ib, cand_cta, false, Time, &ctl->cnt[ib], sd, sm);  // count sources
+                        launch<D, W, TRACE>(P, g, ib, cand_cta, false, Time, (uint32_t)pass + 1u, &ctl->cnt[ib], sd, sm);  // count sources
                         __syncthreads();
                         cursor_close(P, sm, ib);
                         flush_stats(sd, &ctl->cnt[ib]);

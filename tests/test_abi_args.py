@@ -1,0 +1,79 @@
+"""Argument checks of the C ABI that need no GPU: every entry point rejects a null handle,
+missing buffers and out-of-range sizes with CSP_ERR_INVALID before it touches CUDA."""
+import ctypes
+
+import numpy as np
+import pytest
+
+INVALID = 1
+vp, i64, i64p = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1511_06441_gb300 import build
+    L = ctypes.CDLL(build.build())
+    L.csp_status_string.restype = ctypes.c_char_p
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(i64p)
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.csp_status_string(code)
+    assert lib.csp_status_string(99)  # unknown codes still get a text
+
+
+@pytest.mark.parametrize("d,wb", [(0, 1), (5, 1), (2, 3), (2, 0)])
+def test_create_lattice_rejects_bad_shapes(lib, d, wb):
+    ext = np.array([4, 4, 4, 4, 4], np.int64)
+    f = np.zeros(5 * 1024, np.uint16)
+    out = vp()
+    assert lib.csp_create_lattice(d, _p(ext), f.ctypes.data_as(vp), f.ctypes.data_as(vp), wb, 0, None,
+                                  ctypes.byref(out)) == INVALID
+    assert not out.value
+
+
+def test_create_lattice_rejects_missing_buffers(lib):
+    ext = np.array([4, 4], np.int64)
+    f = np.zeros(32, np.uint8)
+    out = vp()
+    assert lib.csp_create_lattice(2, None, f.ctypes.data_as(vp), f.ctypes.data_as(vp), 1, 0, None,
+                                  ctypes.byref(out)) == INVALID
+    assert lib.csp_create_lattice(2, _p(ext), None, f.ctypes.data_as(vp), 1, 0, None, ctypes.byref(out)) == INVALID
+    assert lib.csp_create_lattice(2, _p(ext), f.ctypes.data_as(vp), f.ctypes.data_as(vp), 1, 0, None, None) == INVALID
+
+
+def test_null_lattice_is_rejected_everywhere(lib):
+    A = np.array([0], np.int64)
+    B = np.array([1], np.int64)
+    res = (ctypes.c_int64 * 16)()
+    path = np.zeros(4, np.int64)
+    n = ctypes.c_int64(0)
+    assert lib.csp_solve(None, _p(A), i64(1), _p(B), i64(1), i64(10), None, ctypes.byref(res), None, i64(0),
+                         None) == INVALID
+    assert lib.csp_solve_async(None, vp(1), i64(1), vp(1), i64(1), i64(10), None, vp(1), None, i64(0)) == INVALID
+    assert lib.csp_reconstruct_path(None, _p(A), i64(1), _p(B), i64(1), i64(10), None, _p(path), i64(4),
+                                    ctypes.byref(n)) == INVALID
+    assert lib.csp_reconstruct_fast(None, _p(A), i64(1), _p(B), i64(1), i64(10), None, i64(0), ctypes.byref(res),
+                                    _p(path), i64(4), ctypes.byref(n)) == INVALID
+    assert lib.csp_reserve(None, i64(0)) == INVALID
+    assert lib.csp_get_labels(None, vp(1)) == INVALID
+    out = vp()
+    assert lib.csp_server_create(None, None, ctypes.byref(out)) == INVALID
+    assert lib.csp_batch_create(None, i64(0), None, ctypes.byref(out)) == INVALID
+
+
+def test_static_entry_point_rejects_bad_shapes(lib):
+    ext = np.array([4, 4], np.int64)
+    A = np.array([0], np.int64)
+    for d, wb, M in [(0, 1, 10), (5, 1, 10), (2, 3, 10), (2, 1, 1 << 31)]:
+        assert lib.csp_solve_static(d, _p(ext), vp(1), vp(1), wb, vp(1), i64(1), vp(1), i64(1), i64(M), i64(0),
+                                    None, vp(1)) == INVALID
+    big = np.array([1 << 28, 1], np.int64)  # too many vertices
+    assert lib.csp_solve_static(2, _p(big), vp(1), vp(1), 1, vp(1), i64(1), vp(1), i64(1), i64(10), i64(0), None,
+                                vp(1)) == INVALID
+    del A

@@ -322,6 +322,8 @@ def run_ours(args):
         line["serving"] = bench_serving(csp, synth, args.serve)
     if world == 1 and args.anticorrelated:
         line["anticorrelated"] = bench_anticorrelated(csp, synth)
+    if world == 1 and args.open_problems:
+        line["open_problems"] = bench_open_problems(csp, synth)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, ORACLE_SAMPLE_CYCLES)
     print(json.dumps(line), flush=True)
@@ -376,6 +378,42 @@ def bench_anticorrelated(csp, synth):
     }
     lat.close()
     torch.cuda.empty_cache()
+    return out
+
+
+def bench_open_problems(csp, synth, seeds=(6, 7, 8, 9), side=1024):
+    """The paper's first open problem (final section): the average size of the active set at
+    time t when travel times and weights are i.i.d. random.  2-D side x side lattices with
+    f1 ~ U{1..16} and water from the centre vertex until it reaches a corner (or dies out);
+    the per-cycle trace (active vertices, live flows) averaged over seeds at t = side/16 ..
+    the end.  Three settings: f2 = 0 (travel times only, first-passage percolation: the
+    setting of the paper's Lemma and Theorem), f2 ~ U{1..16} with a bound that never binds,
+    and f2 ~ U{1..16} with M = 2 side (water dies out before the corners)."""
+    out = {"workload": f"lattice2d_{side}_U16_point_source_B_corners", "seeds": list(seeds), "cases": []}
+    for name, M, zero_f2 in (("f2 = 0", 1, True), ("f2 ~ U{1..16}, M never binds", (1 << 31) - 2, False),
+                             (f"f2 ~ U{{1..16}}, M = {2 * side}", 2 * side, False)):
+        traces = []
+        for seed in seeds:
+            inst = synth.workload_point_source(side, seed)
+            f2 = np.zeros_like(inst.f2) if zero_f2 else inst.f2
+            lat = csp.Lattice(inst.extents, inst.f1, f2)
+            r = lat.solve(inst.A, inst.B, M, trace=True, trace_cap=1 << 17)
+            traces.append(r.trace)
+            lat.close()
+        t_end = min(int(tr[-1, 0]) for tr in traces)
+        rows = []
+        t = side // 16
+        while t <= t_end:
+            act, flo = [], []
+            for tr in traces:
+                k = int(np.searchsorted(tr[:, 0], t, side="right")) - 1  # the state at time t
+                act.append(int(tr[k, 1]))
+                flo.append(int(tr[k, 2]))
+            ma = float(np.mean(act))
+            rows.append({"t": t, "mean_active": ma, "active_per_t": ma / t,
+                         "flows_per_active": float(np.sum(flo)) / max(1, float(np.sum(act)))})
+            t *= 2
+        out["cases"].append({"case": name, "M": M, "end_time_min_over_seeds": t_end, "rows": rows})
     return out
 
 
@@ -502,6 +540,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=1, help="also measure 512 batched instances vs one launch each (N=1)")
+    ap.add_argument("--open-problems", type=int, default=0,
+                    help="also measure the mean active-set size vs time on 1024^2 i.i.d. lattices (N=1)")
     ap.add_argument("--anticorrelated", type=int, default=1,
                     help="also time the 4096^2 anti-correlated solve and its path (N=1; ~1.5 min)")
     ap.add_argument("--serve", type=int, default=2000,

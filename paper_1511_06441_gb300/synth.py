@@ -223,6 +223,16 @@ def workload_cube(side: int = 128, M: int = 1600, seed: int = 2) -> Instance:
                     f"cube3d_{side}_M{M}")
 
 
+def workload_point_source(side: int = 1024, seed: int = 6) -> Instance:
+    """2-D side x side, f1,f2 ~ U{1..16} uint8, A = the centre vertex, B = the four corners
+    (the set-up for measuring how the active set grows with time; M is the caller's)."""
+    ext = [side, side]
+    f1, f2 = uniform_weights(ext, 1, 16, seed)
+    c = (side // 2) + (side // 2) * side
+    B = np.array([0, side - 1, side * (side - 1), side * side - 1], np.int64)
+    return Instance(ext, f1, f2, np.array([c], np.int64), B, 0, f"lattice2d_{side}_U16_point_source")
+
+
 def anticorrelated_weights(extents: Sequence[int], seed: int = 3):
     """f1 = min(255, Geometric(0.1)), f2 = 256 - f1, stored as uint16; upper faces zeroed."""
     d, V = len(extents), num_vertices(extents)

@@ -90,3 +90,10 @@ def test_face_matches_coordinates():
         for c in (0, ext[k] - 1):
             want = np.nonzero(synth.coords(np.arange(60), ext)[:, k] == c)[0]
             np.testing.assert_array_equal(synth.face(ext, k, c), want)
+
+
+def test_point_source_workload():
+    inst = synth.workload_point_source(16, seed=6)
+    assert inst.A.tolist() == [8 + 8 * 16]
+    assert sorted(inst.B.tolist()) == [0, 15, 240, 255]
+    assert inst.f1.dtype == np.uint8 and 1 <= inst.f1[0, 0] <= 16

@@ -382,8 +382,8 @@ def bench_anticorrelated(csp, synth):
 
 
 def bench_open_problems(csp, synth, seeds=(6, 7, 8, 9), side=1024):
-    """The paper's first open problem (final section): the average size of the active set at
-    time t when travel times and weights are i.i.d. random.  2-D side x side lattices with
+    """The paper's open problems (final section): the average size of the active set at time t,
+    and the number of phantoms created, when travel times and weights are i.i.d. random.  2-D side x side lattices with
     f1 ~ U{1..16} and water from the centre vertex until it reaches a corner (or dies out);
     the per-cycle trace (active vertices, live flows) averaged over seeds at t = side/16 ..
     the end.  Three settings: f2 = 0 (travel times only, first-passage percolation: the
@@ -392,13 +392,15 @@ def bench_open_problems(csp, synth, seeds=(6, 7, 8, 9), side=1024):
     out = {"workload": f"lattice2d_{side}_U16_point_source_B_corners", "seeds": list(seeds), "cases": []}
     for name, M, zero_f2 in (("f2 = 0", 1, True), ("f2 ~ U{1..16}, M never binds", (1 << 31) - 2, False),
                              (f"f2 ~ U{{1..16}}, M = {2 * side}", 2 * side, False)):
-        traces = []
+        traces, ph, la = [], [], []
         for seed in seeds:
             inst = synth.workload_point_source(side, seed)
             f2 = np.zeros_like(inst.f2) if zero_f2 else inst.f2
             lat = csp.Lattice(inst.extents, inst.f1, f2)
-            r = lat.solve(inst.A, inst.B, M, trace=True, trace_cap=1 << 17)
+            r = lat.solve(inst.A, inst.B, M, trace=True, trace_cap=1 << 17, phantoms=True)
             traces.append(r.trace)
+            ph.append(r.phantoms)
+            la.append(r.launched)
             lat.close()
         t_end = min(int(tr[-1, 0]) for tr in traces)
         rows = []
@@ -413,7 +415,9 @@ def bench_open_problems(csp, synth, seeds=(6, 7, 8, 9), side=1024):
             rows.append({"t": t, "mean_active": ma, "active_per_t": ma / t,
                          "flows_per_active": float(np.sum(flo)) / max(1, float(np.sum(act)))})
             t *= 2
-        out["cases"].append({"case": name, "M": M, "end_time_min_over_seeds": t_end, "rows": rows})
+        out["cases"].append({"case": name, "M": M, "end_time_min_over_seeds": t_end, "rows": rows,
+                             "mean_phantoms_per_solve": float(np.mean(ph)),
+                             "phantoms_per_launched_flow": float(np.sum(ph)) / max(1, float(np.sum(la)))})
     return out
 
 

@@ -59,6 +59,9 @@ typedef struct {
     int64_t max_pool;  /* largest flow-pool size seen */
     int64_t arrivals;  /* flows that delivered water (each improved its destination) */
     int64_t improved;  /* label improvements = sum over cycles of the triggered vertices */
+    int64_t phantoms;  /* flows started on a directed edge that already carried one (the paper's
+                          phantom edges, Step 5); counted only with a trace and CSP_OPT_PHANTOMS,
+                          else -1 */
 } csp_result;
 
 typedef struct {
@@ -73,7 +76,13 @@ typedef struct {
     void *stream;           /* cudaStream_t to run on; NULL = the legacy default stream */
     void *ev_begin;         /* nullable cudaEvent_t recorded on the stream just before the cycle kernel */
     void *ev_end;           /* nullable cudaEvent_t recorded just after it */
+    int32_t flags;          /* CSP_OPT_* bits */
+    int32_t reserved;       /* 0 */
 } csp_options;
+
+/* csp_options.flags: with a trace, also count phantoms (csp_result.phantoms); costs a store
+ * per staying flow and a load per started flow in every cycle. */
+#define CSP_OPT_PHANTOMS 1
 
 /* Text for a status code (static storage). */
 const char *csp_status_string(csp_status s);
@@ -127,7 +136,7 @@ csp_status csp_solve(csp_lattice *lat, const int64_t *A, int64_t nA, const int64
  * Asynchronous solve with device-resident sets: enqueues the whole solve on opt->stream
  * and returns without waiting.  A_dev, B_dev are device arrays of int64 ids.  The result
  * is written to result_dev (device, 16 int64: status, F1, X, x_src, x_dir, F2, cycles,
- * updates, launched, passes, max_pool, trace_len, elapsed_ns, arrivals, improved, 0;
+ * updates, launched, passes, max_pool, trace_len, elapsed_ns, arrivals, improved, phantoms;
  * elapsed_ns = device time of the cycle loop, from %globaltimer).  Invalid ids, A and B not
  * disjoint, pool overflow etc. are reported in result_dev[0], not by the return value
  * (which reports only host-side argument errors and launch failures).  trace_dev:

@@ -88,6 +88,7 @@ class Result:
     cycles: int = -1
     updates: int = -1          # sum over cycles of the flows alive at cycle start
     launched: int = -1         # flows started (including phantoms)
+    phantoms: int = -1         # flows started on a directed edge that already carried one (O1 only)
     trace: Optional[np.ndarray] = None     # (rows, 3) int64: Time, active vertices, flows
     labels: Optional[np.ndarray] = None    # (V,) int64 labels at termination
     snapshot: Optional[np.ndarray] = None  # active vertex ids at the requested time
@@ -120,7 +121,7 @@ def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 <
     if removed is not None:
         rem = np.zeros(V, np.uint8)
         rem[np.asarray(removed, dtype=np.int64)] = 1
-    res = np.zeros(8, np.int64)
+    res = np.zeros(9, np.int64)
     cap = 1 << 12
     while True:
         tr = np.zeros(3 * cap if trace else 3, np.int64)
@@ -141,7 +142,7 @@ def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 <
         if not trace or tl[0] <= cap:
             break
         cap = int(tl[0])
-    return Result(*[int(x) for x in res[:8]],
+    return Result(*[int(x) for x in res[:9]],
                   trace=tr[: 3 * int(tl[0])].reshape(-1, 3) if trace else None,
                   labels=lab,
                   snapshot=snap[: int(sl[0])] if snap is not None else None)

@@ -153,8 +153,10 @@ static int flows_push(flows_t *F, flow_t f)
 
 /* Start a flow on every edge (v, u) along which water of quality Label(v) would still
  * raise Label(u): Label(v) - f2 > Label(u) (Step 4, TriggerEdges; Step 5 creates the
- * flow, a phantom if the edge already carries water). */
-static int launch_from(const lattice_t *L, const int64_t *label, int64_t v, flows_t *F, int64_t *launched)
+ * flow, a phantom if the edge already carries water).  on_edge[v * 2d + dir] counts the
+ * flows on each directed edge; a flow started while it is positive is a phantom. */
+static int launch_from(const lattice_t *L, const int64_t *label, int64_t v, flows_t *F, int64_t *launched,
+                       int64_t *on_edge, int64_t *phantoms)
 {
     for (int dir = 0; dir < 2 * L->d; dir++) {
         int64_t t, w;
@@ -164,17 +166,22 @@ static int launch_from(const lattice_t *L, const int64_t *label, int64_t v, flow
             flow_t f = {v, dir, u, label[v], w, t};
             if (flows_push(F, f)) return OR_OOM;
             (*launched)++;
+            int64_t *c = &on_edge[v * 2 * L->d + dir];
+            if (*c > 0) (*phantoms)++;
+            (*c)++;
         }
     }
     return OR_OK;
 }
 
 /* Steps 7-9: drop every flow that can no longer improve its destination. */
-static void prune(flows_t *F, const int64_t *label)
+static void prune(flows_t *F, const int64_t *label, int64_t *on_edge, int twod)
 {
     int64_t j = 0;
-    for (int64_t i = 0; i < F->n; i++)
+    for (int64_t i = 0; i < F->n; i++) {
         if (F->a[i].Q - F->a[i].f2 > label[F->a[i].dst]) F->a[j++] = F->a[i];
+        else on_edge[F->a[i].src * twod + F->a[i].dir]--;
+    }
     F->n = j;
 }
 
@@ -200,8 +207,10 @@ static int cmp_i64(const void *x, const void *y)
 }
 
 /*
- * O1.  res[0..7] = F1, X, x_src, x_dir, F2, cycles, updates, flows_launched, where
- * updates = sum over cycles of the flows alive when the cycle starts.  trace receives
+ * O1.  res[0..8] = F1, X, x_src, x_dir, F2, cycles, updates, flows_launched, phantoms,
+ * where updates = sum over cycles of the flows alive when the cycle starts and phantoms
+ * = flows started on a directed edge that already carried a flow (after the arrivals of
+ * the cycle, before its removals: the paper's phantom edges, Step 5).  trace receives
  * rows (Time, active vertices, flows) after the removals of each cycle, row 0 being the
  * state after initialisation; *trace_len is the number of rows produced (it may exceed
  * trace_cap, then only trace_cap rows are written).  If snap is not NULL it receives the
@@ -229,9 +238,11 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
     int64_t *touched = malloc((size_t)V * sizeof(int64_t));
     int64_t *improved = malloc((size_t)V * sizeof(int64_t));
     int64_t *xsrc = malloc((size_t)V * sizeof(int64_t)), *xdir = malloc((size_t)V * sizeof(int64_t));
+    int64_t *on_edge = calloc((size_t)V * 2 * d, sizeof(int64_t));
     flows_t F = {0, 0, 0};
-    int64_t rows = 0, Time = 0, cycles = 0, updates = 0, launched = 0;
-    if (!inA || !inB || !label || !stamp || !bq || !bsrc || !bdir || !touched || !improved || !xsrc || !xdir) {
+    int64_t rows = 0, Time = 0, cycles = 0, updates = 0, launched = 0, phantoms = 0;
+    if (!inA || !inB || !label || !stamp || !bq || !bsrc || !bdir || !touched || !improved || !xsrc || !xdir ||
+        !on_edge) {
         rc = OR_OOM;
         goto done;
     }
@@ -247,15 +258,15 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
         stamp[v] = -1;
         bq[v] = INT64_MIN;
     }
-    for (int i = 0; i < 8; i++) res[i] = -1;
+    for (int i = 0; i < 9; i++) res[i] = -1;
     if (snap_len) *snap_len = 0;
 
     /* Initialization (Algorithm 3): Label = M on A, 0 elsewhere; water leaves A. */
     for (int64_t v = 0; v < V; v++)
         if (inA[v]) label[v] = M;
     for (int64_t v = 0; v < V; v++)
-        if (inA[v] && (rc = launch_from(&L, label, v, &F, &launched))) goto done;
-    prune(&F, label);
+        if (inA[v] && (rc = launch_from(&L, label, v, &F, &launched, on_edge, &phantoms))) goto done;
+    prune(&F, label, on_edge, 2 * d);
     {
         int64_t act = count_active(&F, stamp, 0, NULL);
         if (rows < trace_cap) {
@@ -290,6 +301,7 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
                 F.a[j++] = *f;
                 continue;
             }
+            on_edge[f->src * 2 * d + f->dir]--;  /* arrived: off the edge */
             int64_t q = f->Q - f->f2, u = f->dst;
             if (bq[u] == INT64_MIN) touched[nt++] = u;
             if (q > bq[u] || (q == bq[u] && (f->src < bsrc[u] || (f->src == bsrc[u] && f->dir < bdir[u])))) {
@@ -314,9 +326,9 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
         qsort(improved, (size_t)ni, sizeof(int64_t), cmp_i64);
         /* Steps 4-5: water leaves every improved vertex (labels of this cycle). */
         for (int64_t i = 0; i < ni; i++)
-            if ((rc = launch_from(&L, label, improved[i], &F, &launched))) goto done;
+            if ((rc = launch_from(&L, label, improved[i], &F, &launched, on_edge, &phantoms))) goto done;
         /* Steps 7-9. */
-        prune(&F, label);
+        prune(&F, label, on_edge, 2 * d);
         int64_t act = count_active(&F, stamp, cycles, NULL);
         if (rows < trace_cap) {
             trace[3 * rows] = Time;
@@ -343,13 +355,14 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
     res[5] = cycles;
     res[6] = updates;
     res[7] = launched;
+    res[8] = phantoms;
     if (rc) goto done;
     if (snap && snap_len && *snap_len > 0) qsort(snap, (size_t)*snap_len, sizeof(int64_t), cmp_i64);
     if (labels_out) memcpy(labels_out, label, (size_t)V * sizeof(int64_t));
 done:
     *trace_len = rows;
     free(inA); free(inB); free(label); free(stamp); free(bq); free(bsrc); free(bdir);
-    free(touched); free(improved); free(xsrc); free(xdir); free(F.a);
+    free(touched); free(improved); free(xsrc); free(xdir); free(F.a); free(on_edge);
     return rc;
 }
 

@@ -33,12 +33,15 @@ vp = ctypes.c_void_p
 class CspResult(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("F1", "X", "x_src", "x_dir", "F2", "cycles", "updates", "launched", "passes", "max_pool",
-                 "arrivals", "improved")]
+                 "arrivals", "improved", "phantoms")]
 
 
 class CspOptions(ctypes.Structure):
     _fields_ = [("max_cycles", ctypes.c_int64), ("pool_capacity", ctypes.c_int64), ("ctas", ctypes.c_int32),
-                ("time_limit_s", ctypes.c_int32), ("stream", vp), ("ev_begin", vp), ("ev_end", vp)]
+                ("time_limit_s", ctypes.c_int32), ("stream", vp), ("ev_begin", vp), ("ev_end", vp),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+OPT_PHANTOMS = 1  # CSP_OPT_PHANTOMS
 
 
 class CspError(RuntimeError):
@@ -115,6 +118,7 @@ class Result:
     max_pool: int
     arrivals: int = -1
     improved: int = -1
+    phantoms: int = -1       # flows started on an edge that already carried one (trace mode), else -1
     status: int = OK
     trace: Optional[np.ndarray] = None
 
@@ -129,9 +133,9 @@ def _event_handle(ev) -> Optional[int]:
 
 
 def options(max_cycles: int = 0, pool_capacity: int = 0, ctas: int = 0, stream=None,
-            ev_begin=None, ev_end=None, time_limit_s: int = 0) -> CspOptions:
+            ev_begin=None, ev_end=None, time_limit_s: int = 0, phantoms: bool = False) -> CspOptions:
     return CspOptions(max_cycles, pool_capacity, ctas, int(time_limit_s), _stream_handle(stream),
-                      _event_handle(ev_begin), _event_handle(ev_end))
+                      _event_handle(ev_begin), _event_handle(ev_end), OPT_PHANTOMS if phantoms else 0, 0)
 
 
 class Lattice:
@@ -184,11 +188,14 @@ class Lattice:
 
     def solve(self, A, B, M: int, *, trace: bool = False, trace_cap: int = 1 << 16, max_cycles: int = 0,
               pool_capacity: int = 0, ctas: int = 0, stream=None, check: bool = True,
-              time_limit_s: int = 0) -> Result:
-        """``csp_solve``: host sets in, host result out (blocks until done)."""
+              time_limit_s: int = 0, phantoms: bool = False) -> Result:
+        """``csp_solve``: host sets in, host result out (blocks until done).
+
+        ``phantoms`` (with ``trace``) also counts the flows started on an edge that already
+        carries one (``Result.phantoms``)."""
         A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
         B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
-        opt = options(max_cycles, pool_capacity, ctas, stream, time_limit_s=time_limit_s)
+        opt = options(max_cycles, pool_capacity, ctas, stream, time_limit_s=time_limit_s, phantoms=phantoms)
         res = CspResult()
         tr = np.zeros(3 * trace_cap, np.int64) if trace else None
         tl = ctypes.c_int64(0)
@@ -261,7 +268,7 @@ def result_from_record(rec) -> Result:
     """Converts a 16-int64 result record (``csp_solve_async``) into a :class:`Result`."""
     r = [int(x) for x in np.asarray(rec).reshape(-1)[:16]]
     return Result(F1=r[1], X=r[2], x_src=r[3], x_dir=r[4], F2=r[5], cycles=r[6], updates=r[7], launched=r[8],
-                  passes=r[9], max_pool=r[10], arrivals=r[13], improved=r[14], status=r[0])
+                  passes=r[9], max_pool=r[10], arrivals=r[13], improved=r[14], phantoms=r[15], status=r[0])
 
 
 def solve_instance(inst, **kw) -> Result:

@@ -510,6 +510,7 @@ csp_status csp_batch_results(csp_batch *b, csp_result *out, int32_t *status, int
         x.max_pool = o[R_MAXPOOL];
         x.arrivals = o[R_ARRIVALS];
         x.improved = o[R_IMPROVED];
+        x.phantoms = o[R_PHANTOMS];
         if (status) status[i] = (int32_t)o[R_STATUS];
         if (elapsed_ns) elapsed_ns[i] = o[R_ELAPSED_NS];
     }

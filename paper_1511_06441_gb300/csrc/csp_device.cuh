@@ -9,6 +9,8 @@
 //                     its high half equals label[] at every cycle boundary
 //   isB[V/32] uint32  bitmap of B
 //   src_stamp uint32  per vertex: the last pass in which it sourced a live flow (trace mode)
+//   edge_stamp uint32 per directed edge (v * 2d + dir): the last pass in which it carried a
+//                     flow that did not arrive (trace mode; phantom count)
 //   cand[]    uint32  arrivals of the current cycle (flow word ed of each arriving flow),
 //                     one region of cand_cap / G entries per CTA of the group
 //   pool[2]   SoA     ed = dst << 3 | direction back to the source (uint32),
@@ -45,7 +47,7 @@ enum : int { ST_OK = 0, ST_INVALID = 1, ST_OOM = 2, ST_CUDA = 3, ST_CAPACITY = 4
 // result record (int64): index of each field
 enum : int {
     R_STATUS = 0, R_F1, R_X, R_XSRC, R_XDIR, R_F2, R_CYCLES, R_UPDATES, R_LAUNCHED, R_PASSES,
-    R_MAXPOOL, R_TRACELEN, R_ELAPSED_NS, R_ARRIVALS, R_IMPROVED, R_COUNT = 16
+    R_MAXPOOL, R_TRACELEN, R_ELAPSED_NS, R_ARRIVALS, R_IMPROVED, R_PHANTOMS, R_COUNT = 16
 };
 
 __host__ __device__ __forceinline__ unsigned int lo32(unsigned long long x) { return (unsigned int)(x & 0xffffffffull); }
@@ -64,6 +66,7 @@ struct Counters {
     alignas(128) unsigned int overflow;        // an output list ran out of room
     unsigned int abort;                        // set by the leader when the solve exceeded its time budget
     alignas(128) unsigned int chunks;          // output-pool chunks handed out in this pass
+    alignas(128) unsigned long long phantoms;  // trace mode: flows started on an edge that carries one
 };
 
 constexpr int NRELEASE = 32;  // copies of the barrier's release word, one per 128-byte line
@@ -113,6 +116,7 @@ struct Params {
     unsigned long long *offer;
     const uint32_t *isB;
     uint32_t *src_stamp;           // trace mode: [V rounded up to 4] last pass each vertex sourced a live flow
+    uint32_t *edge_stamp;          // nullable (trace mode, phantom count): [2d V] last pass each directed edge carried a staying flow
     uint32_t *cand;                // arrivals of the current cycle (the sources of A at the seed)
     unsigned int cand_cap;
     uint32_t *ed[2];
@@ -346,26 +350,27 @@ __device__ __forceinline__ void drain_stages(Smem &sm, const uint32_t (&parity)[
 }
 
 struct LocalStats {
-    uint32_t live, launched, improved, active, written, cands;
+    uint32_t live, launched, improved, active, written, cands, phantoms;
     int min_ta;
 };
 
 // Adds this block's statistics to the pass counters (one global atomic per word per CTA).
 __device__ __forceinline__ void flush_stats(const LocalStats &st, Counters *C)
 {
-    __shared__ unsigned long long s_live, s_li, s_oc;
+    __shared__ unsigned long long s_live, s_li, s_oc, s_ph;
     __shared__ unsigned int s_act;
     __shared__ int s_min;
     if (threadIdx.x == 0) {
         s_live = 0;
         s_li = 0;
         s_oc = 0;
+        s_ph = 0;
         s_act = 0;
         s_min = INT_MAX;
     }
     __syncthreads();
     uint32_t live = st.live, lau = st.launched, imp = st.improved, act = st.active, wr = st.written,
-             cd = st.cands;
+             cd = st.cands, ph = st.phantoms;
     int mn = st.min_ta;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -375,6 +380,7 @@ __device__ __forceinline__ void flush_stats(const LocalStats &st, Counters *C)
         act += __shfl_xor_sync(0xffffffffu, act, o);
         wr += __shfl_xor_sync(0xffffffffu, wr, o);
         cd += __shfl_xor_sync(0xffffffffu, cd, o);
+        ph += __shfl_xor_sync(0xffffffffu, ph, o);
         mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     }
     if ((threadIdx.x & 31) == 0) {
@@ -382,6 +388,7 @@ __device__ __forceinline__ void flush_stats(const LocalStats &st, Counters *C)
         if (lau | imp) atomicAdd(&s_li, (unsigned long long)lau | ((unsigned long long)imp << 32));
         if (wr | cd) atomicAdd(&s_oc, (unsigned long long)wr | ((unsigned long long)cd << 32));
         if (act) atomicAdd(&s_act, act);
+        if (ph) atomicAdd(&s_ph, (unsigned long long)ph);
         if (mn != INT_MAX) atomicMin(&s_min, mn);
     }
     __syncthreads();
@@ -390,6 +397,7 @@ __device__ __forceinline__ void flush_stats(const LocalStats &st, Counters *C)
         if (s_li) atomicAdd(&C->lau_imp, s_li);
         if (s_oc) atomicAdd(&C->out_cand, s_oc);
         if (s_act) atomicAdd(&C->n_active, s_act);
+        if (s_ph) atomicAdd(&C->phantoms, s_ph);
         if (s_min != INT_MAX) atomicMin(&C->min_ta, s_min);
     }
 }
@@ -620,6 +628,11 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
                 } else {
                     keep = true;
                     st.min_ta = min(st.min_ta, t);
+                    if (TRACE && P.edge_stamp) {  // this directed edge still carries a flow when the cycle launches
+                        const uint32_t r = e[i] & 7u;
+                        const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(P.stride, r));
+                        P.edge_stamp[(size_t)src * (2 * D) + (r ^ 1u)] = stamp;
+                    }
                 }
             }
             bk[i] = __ballot_sync(0xffffffffu, keep);
@@ -809,6 +822,12 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
                 if ((bw >> (v & 31)) & 1u)
                     atomicMax(&C->xkey, ((unsigned long long)(uint32_t)Lv << 32) | (0xffffffffu - v));
                 mask = launch_mask<W, D>(r, Lv, Lw);
+                if (TRACE && P.edge_stamp) {  // a flow started on an edge that still carries one is a phantom (Step 5)
+#pragma unroll
+                    for (int dir = 0; dir < 2 * D; dir++)
+                        if ((mask >> dir) & 1u)
+                            st.phantoms += __ldcg(P.edge_stamp + (size_t)v * (2 * D) + dir) == stamp;
+                }
             }
         }
         if (P.log) {  // every improvement, in this pass's segment of the log
@@ -874,13 +893,14 @@ __device__ __forceinline__ void zero_counters(Counters *c)
 {
     c->out_cand = c->live = c->lau_imp = c->xkey = 0;
     c->n_active = c->overflow = c->abort = c->chunks = 0;
+    c->phantoms = 0;
     c->min_ta = INT_MAX;
 }
 
 // A snapshot of one pass's counters, read by every CTA after the pass's last barrier.
 struct PassCounts {
     unsigned int n_out, n_cand, launched, improved, n_active, overflow, abort, chunks;
-    unsigned long long n_live, xkey;
+    unsigned long long n_live, xkey, phantoms;
     int min_ta;
 };
 
@@ -897,6 +917,7 @@ __device__ __forceinline__ PassCounts read_counters(const Counters *c)
         const unsigned int act = __ldcg(&c->n_active), ovf = __ldcg(&c->overflow), ab = __ldcg(&c->abort);
         const int mt = __ldcg(&c->min_ta);
         s_pc.chunks = __ldcg(&c->chunks);
+        s_pc.phantoms = __ldcg(&c->phantoms);
         s_pc.n_out = lo32(oc);
         s_pc.n_cand = hi32(oc);
         s_pc.launched = lo32(li);
@@ -939,7 +960,8 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
     const int M = P.M;
     const unsigned long long t_start = globaltimer_ns();
 
-    long long cycle = 0, updates = 0, launched = 0, passes = 0, trace_len = 0, arrivals = 0, improved = 0;
+    long long cycle = 0, updates = 0, launched = 0, passes = 0, trace_len = 0, arrivals = 0, improved = 0,
+              phantoms = 0;
     unsigned int max_pool = 0;
     int Time = 0, status = ST_OK;
     bool feasible = false;
@@ -960,7 +982,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
         const uint32_t cand_cta = P.cand_cap / g.size;  // candidate region of each CTA
         const uint32_t cand_base = g.rank * cand_cta;
         // seed: water leaves A at Time 0 along every edge that can raise a label
-        LocalStats st{0, 0, 0, 0, 0, 0, INT_MAX};
+        LocalStats st{0, 0, 0, 0, 0, 0, 0, INT_MAX};
         const uint32_t n_src = min(hi32(read_shared_u64(&ctl->cnt[0].out_cand)), P.cand_cap);
         // (the seed adds the flows it writes to the low half of out_cand; the high half keeps n_src)
         if (threadIdx.x == 0) cursor_open(sm);
@@ -986,7 +1008,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
         for (long long pass = 1;; pass++) {
             const int ib = (int)((pass - 1) & 1), ob = ib ^ 1;
             Counters *C = &ctl->cnt[ob];
-            LocalStats sa{0, 0, 0, 0, 0, 0, INT_MAX};
+            LocalStats sa{0, 0, 0, 0, 0, 0, 0, INT_MAX};
             if (threadIdx.x == 0) cursor_open(sm);
             if (!sweep<D, W, TRACE>(P, g, ib, n_tiles, Tg, (uint32_t)pass, C, sa, sm, parity, cand_base, cand_cta)) {
                 status = ST_BARRIER;
@@ -1000,7 +1022,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                 P.pass_off[pass] = *(volatile unsigned long long *)P.log_n;
             }
             if (leader && globaltimer_ns() - t_start > P.budget_ns) C->abort = 1u;  // read by all after the barrier
-            LocalStats sb{0, 0, 0, 0, 0, 0, INT_MAX};
+            LocalStats sb{0, 0, 0, 0, 0, 0, 0, INT_MAX};
             launch<D, W, TRACE>(P, g, ob, cand_cta, true, Tg, (uint32_t)pass, C, sb, sm);
             __syncthreads();
             cursor_close(P, sm, ob);
@@ -1012,6 +1034,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             launched += (long long)c.launched;
             arrivals += (long long)c.n_cand;
             improved += (long long)c.improved;
+            phantoms += (long long)c.phantoms;
             if (c.overflow) { status = ST_CAPACITY; goto finish; }
             if (c.abort) {  // rows 0 .. cycle - 1 are complete
                 status = ST_TIMEOUT;
@@ -1028,7 +1051,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                     xkey = c.xkey;
                     if (TRACE) {
                         // the terminal cycle's row: count the flows still alive after it
-                        LocalStats sc{0, 0, 0, 0, 0, 0, INT_MAX};
+                        LocalStats sc{0, 0, 0, 0, 0, 0, 0, INT_MAX};
                         const uint32_t nt = min(c.chunks, n_chunks);
                         if (threadIdx.x == 0) cursor_open(sm);
                         if (!sweep<D, W, TRACE>(P, g, ob, nt, -1, (uint32_t)pass + 1u, &ctl->cnt[ib], sc, sm, parity, cand_base,
@@ -1038,7 +1061,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                         }
                         flush_stats(sc, &ctl->cnt[ib]);
                         if (!group_sync(ctl, epoch, g, P.barrier_ns)) { status = ST_BARRIER; goto finish; }
-                        LocalStats sd{0, 0, 0, 0, 0, 0, INT_MAX};
+                        LocalStats sd{0, 0, 0, 0, 0, 0, 0, INT_MAX};
                         launch<D, W, TRACE>(P, g, ib, cand_cta, false, Time, (uint32_t)pass + 1u, &ctl->cnt[ib], sd, sm);  // count sources
                         __syncthreads();
                         cursor_close(P, sm, ib);
@@ -1096,6 +1119,7 @@ finish:
         o[R_TRACELEN] = TRACE ? trace_len : 0;
         o[R_ARRIVALS] = arrivals;
         o[R_IMPROVED] = improved;
+        o[R_PHANTOMS] = TRACE && P.edge_stamp ? phantoms : -1;
         o[R_ELAPSED_NS] = (long long)(globaltimer_ns() - t_start);
         if (P.result_dev)
             for (int i = 0; i < R_COUNT; i++) P.result_dev[i] = o[i];
@@ -1143,6 +1167,7 @@ __device__ bool group_setup_sets(const Params<W> &P, const Group &g, const int64
             Counters &c = ctl->cnt[b];
             c.out_cand = c.live = c.lau_imp = c.xkey = 0;
             c.n_active = c.overflow = c.abort = c.chunks = 0;
+            c.phantoms = 0;
             c.min_ta = INT_MAX;
         }
     }

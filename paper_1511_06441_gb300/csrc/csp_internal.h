@@ -41,7 +41,7 @@ struct csp_lattice {
     int64_t pool_cap = 0;
     int32_t *label = nullptr;
     unsigned long long *offer = nullptr;
-    uint32_t *isB = nullptr, *src_stamp = nullptr;
+    uint32_t *isB = nullptr, *src_stamp = nullptr, *edge_stamp = nullptr;
     uint32_t *cand = nullptr;
     int64_t cand_cap = 0;
     uint32_t *ed[2] = {nullptr, nullptr};

@@ -256,6 +256,7 @@ void copy_result(const long long *o, csp_result *x, int32_t *status)
     x->max_pool = o[R_MAXPOOL];
     x->arrivals = o[R_ARRIVALS];
     x->improved = o[R_IMPROVED];
+    x->phantoms = o[R_PHANTOMS];
     if (status) *status = (int32_t)o[R_STATUS];
 }
 

@@ -326,7 +326,7 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
     // can run out of room (a CTA lists at most the flows of its ceil(chunks / CTAs) chunks)
     const int64_t cand_cap = std::max<int64_t>(V, pool_cap + (int64_t)max_group_ctas(L->device) * TILE);
     const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
-                 o_stamp = take(((V + 3) / 4) * 16), o_cand = take(cand_cap * 4), o_ctl = take(sizeof(Control)),
+                 o_stamp = take(((V + 3) / 4) * 16), o_estamp = take(2 * L->d * V * 4), o_cand = take(cand_cap * 4), o_ctl = take(sizeof(Control)),
                  o_trace = take(trace_cap * 24), o_sets = take(sets_cap * 8);
     size_t o_pool[2][3], o_fill[2];
     for (int b = 0; b < 2; b++) {
@@ -347,6 +347,7 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
     L->offer = (unsigned long long *)(b + o_offer);
     L->isB = (uint32_t *)(b + o_isB);
     L->src_stamp = (uint32_t *)(b + o_stamp);
+    L->edge_stamp = (uint32_t *)(b + o_estamp);
     L->cand = (uint32_t *)(b + o_cand);
     L->cand_cap = cand_cap;
     L->ctl = (Control *)(b + o_ctl);
@@ -383,7 +384,9 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
     CSP_CUDA(cudaMemsetAsync(L->label, 0, V * 4, s));
     CSP_CUDA(cudaMemsetAsync(L->offer, 0, V * 8, s));
     CSP_CUDA(cudaMemsetAsync(L->isB, 0, ((V + 31) / 32) * 4, s));
+    const bool phantoms = trace_dev && opt && (opt->flags & CSP_OPT_PHANTOMS);
     if (trace_dev) CSP_CUDA(cudaMemsetAsync(L->src_stamp, 0, ((V + 3) / 4) * 16, s));  // stamps are pass numbers >= 1
+    if (phantoms) CSP_CUDA(cudaMemsetAsync(L->edge_stamp, 0, 2 * L->d * V * 4, s));
     const int sms = num_sms(L->device);
     k_reset<<<1, 32, 0, s>>>(L->ctl);
     k_mark_B<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nB + 255) / 256)), 256, 0, s>>>(B_dev, nB, L->isB, V,
@@ -426,6 +429,7 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         P.offer = L->offer;
         P.isB = L->isB;
         P.src_stamp = L->src_stamp;
+        P.edge_stamp = phantoms ? L->edge_stamp : nullptr;
         P.cand = L->cand;
         P.cand_cap = (unsigned int)L->cand_cap;
         for (int b = 0; b < 2; b++) {
@@ -678,6 +682,7 @@ static csp_status solve_host(csp_lattice *L, const int64_t *A, int64_t nA, const
         out->max_pool = o[R_MAXPOOL];
         out->arrivals = o[R_ARRIVALS];
         out->improved = o[R_IMPROVED];
+        out->phantoms = o[R_PHANTOMS];
         if (trace) {
             const int64_t rows = std::min<int64_t>(o[R_TRACELEN], trace_cap);
             if (rows > 0) CSP_CUDA(cudaMemcpy(trace, L->trace, rows * 24, cudaMemcpyDeviceToHost));

@@ -11,6 +11,8 @@ its definition in the paper:
   by time t of M - F2; a flow leaves v along (v, u) at every time t0 at which L(v)
   improves and is alive at the end of cycle T iff t0 <= T < t0 + f1 and
   L_t0(v) - f2 > L_T(u).
+* :func:`phantoms` - the flows started on an edge that already carries one, from the same
+  label histories (the paper's phantom edges, Step 5).
 * :func:`dijkstra_trace` - for f2 = 0 the problem is first-passage percolation: F1 is the
   Dijkstra distance tau (computed by scipy) and the state at time T is {tau <= T}.
 """
@@ -79,6 +81,62 @@ def brute_force(inst) -> Tuple[int, int, int, int, int]:
         return (-1, -1, -1, -1, -1)
     t, w, end, prev, dr = best
     return (t, end, prev, dr, w)
+
+
+def label_histories(inst):
+    """Per vertex, the times and labels at which its label improves (A: M at time 0), from
+    the (F1, F2) of all simple paths; the time F1 of the first improvement of a B vertex
+    (None if none)."""
+    M = int(inst.M)
+    adj, V = directed_edges(inst.extents, inst.f1, inst.f2)
+    Aset = set(int(a) for a in inst.A)
+    Bset = set(int(b) for b in inst.B)
+    arrivals: Dict[int, List[Tuple[int, int]]] = collections.defaultdict(list)
+    for end, t, w, _, _ in all_simple_paths(inst):
+        if M - w > 0:
+            arrivals[end].append((t, M - w))
+    improvements: Dict[int, List[Tuple[int, int]]] = {}
+    for v in range(V):
+        if v in Aset:
+            improvements[v] = [(0, M)] if M > 0 else []
+            continue
+        hist, cur = [], 0
+        for t, q in sorted(arrivals.get(v, [])):
+            if q > cur:
+                if hist and hist[-1][0] == t:
+                    hist[-1] = (t, q)
+                else:
+                    hist.append((t, q))
+                cur = q
+        improvements[v] = hist
+    F1 = min((improvements[b][0][0] for b in Bset if improvements[b]), default=None)
+    return adj, V, improvements, F1
+
+
+def phantoms(inst) -> int:
+    """Flows started on a directed edge that already carries one (the paper's phantom edges,
+    Step 5): a launch from v along (v, u) at time t0 (v improves at t0 and its new label
+    minus f2 beats Label(u) at the end of t0) is a phantom if an earlier launch on (v, u) at
+    t1 has not arrived (t1 + f1 > t0) and survived the removals up to the cycle before t0
+    (its quality minus f2 still beats Label(u) there).  Launches happen up to F1."""
+    adj, V, improvements, F1 = label_histories(inst)
+
+    def label_at(v, T):
+        lab = 0
+        for t, q in improvements[v]:
+            if t <= T:
+                lab = q
+        return lab
+
+    n = 0
+    for v in range(V):
+        for u, _, t1, w1 in adj.get(v, ()):
+            launches = [(t0, q0) for t0, q0 in improvements[v]
+                        if (F1 is None or t0 <= F1) and q0 - w1 > label_at(u, t0)]
+            for i, (t0, _) in enumerate(launches):
+                if any(ta + t1 > t0 and qa - w1 > label_at(u, t0 - 1) for ta, qa in launches[:i]):
+                    n += 1
+    return n
 
 
 def pareto_trace(inst) -> np.ndarray:

@@ -49,9 +49,10 @@ def test_128_whole_result_equals_cycle_oracle(csp, golden):
     inst = _instance(128, golden)
     want = oracle.cycle(inst.extents, inst.f1, inst.f2, inst.A, inst.B, inst.M, labels=True)
     lat = csp.Lattice(inst.extents, inst.f1, inst.f2)
-    got = lat.solve(inst.A, inst.B, inst.M, trace=True, trace_cap=4096)
+    got = lat.solve(inst.A, inst.B, inst.M, trace=True, trace_cap=4096, phantoms=True)
     assert got.answer() == want.answer()
-    assert (got.cycles, got.updates, got.launched) == (want.cycles, want.updates, want.launched)
+    assert (got.cycles, got.updates, got.launched, got.phantoms) == (want.cycles, want.updates, want.launched,
+                                                                     want.phantoms)
     np.testing.assert_array_equal(got.trace, want.trace)
     np.testing.assert_array_equal(lat.labels(), want.labels.astype(np.int32))
     g = golden["128"]

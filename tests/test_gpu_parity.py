@@ -2,7 +2,7 @@
 
 All results are integers and must match exactly: F1, X, x, F2, the cycle count, the
 active-edge update count, the number of flows started, the per-cycle trace (Time,
-active vertices, live flows) and the final label array.
+active vertices, live flows), the phantom count and the final label array.
 
 Sizes: tiny random lattices (1 CTA and several CTAs, so every barrier and compaction
 path runs on ragged tails), medium lattices spanning many 2048-flow tiles, the 64x64
@@ -37,6 +37,8 @@ def _check_same(lat, got, want, trace=True, labels=True):
     assert (got.cycles, got.updates, got.launched) == (want.cycles, want.updates, want.launched)
     if trace:
         np.testing.assert_array_equal(got.trace, want.trace)
+        if got.phantoms >= 0:  # counted when requested (trace mode)
+            assert got.phantoms == want.phantoms
     if labels:
         np.testing.assert_array_equal(lat.labels(), want.labels.astype(np.int32))
 
@@ -45,7 +47,7 @@ def _run_pair(csp, inst, ctas=0, M=None, **kw):
     M = inst.M if M is None else M
     want = oracle.cycle(inst.extents, inst.f1, inst.f2, inst.A, inst.B, M, labels=True)
     lat = csp.Lattice(inst.extents, inst.f1, inst.f2)
-    got = lat.solve(inst.A, inst.B, M, trace=True, ctas=ctas, **kw)
+    got = lat.solve(inst.A, inst.B, M, trace=True, ctas=ctas, phantoms=True, **kw)
     _check_same(lat, got, want)
     lat.close()
     return got, want

@@ -258,3 +258,27 @@ def test_lexmin_path_on_anticorrelated_lattice_matches_repeated_application():
     inst.M = (12 * F2) // 10
     want, _ = oracle.reconstruct(inst.extents, inst.f1, inst.f2, inst.A, inst.B, inst.M)
     assert path == want and path[0] == 0 and path[-1] == X
+
+
+# ---------------------------------------------------------------- phantoms (Step 5)
+
+def test_o1_phantoms_equal_brute_force():
+    """Flows started on an edge that already carries one, counted by O1 (per-edge counts of
+    live flows) against the definition on all simple paths' label histories."""
+    with_phantoms = 0
+    for seed in range(4000, 4300):
+        inst = _tiny(seed, max_vertices=18, dims=(2,), f_lo=(0,), f_hi=12, absent_prob=0.0)
+        inst.M = 80
+        want = brute.phantoms(inst)
+        assert oracle.solve_instance(inst).phantoms == want, seed
+        with_phantoms += want > 0
+    assert with_phantoms >= 20  # the comparison is not vacuous
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_no_phantoms_when_weights_are_zero(seed):
+    """With f2 = 0 every label jumps to M at its first arrival and never improves again, so no
+    vertex starts a second flow on an edge."""
+    inst = synth.workload_point_source(48, seed=seed)
+    r = oracle.cycle(inst.extents, inst.f1, np.zeros_like(inst.f2), inst.A, inst.B, 1, trace=False)
+    assert r.phantoms == 0 and r.launched > 0

@@ -34,7 +34,7 @@ extern "C" {
 
 typedef enum {
     CSP_OK = 0,
-    CSP_ERR_INVALID = 1,  /* bad argument: d, extents, ids out of range, A and B not disjoint, empty A or B, M >= 2^31 */
+    CSP_ERR_INVALID = 1,  /* bad argument: d, extents, ids out of range, A and B not disjoint, empty A or B, M >= 2^31 - 1 */
     CSP_ERR_OOM = 2,      /* device or host allocation failed */
     CSP_ERR_CUDA = 3,     /* a CUDA call failed; csp_last_error() has the text */
     CSP_ERR_CAPACITY = 4, /* the flow pool overflowed, or arrival times would reach 2^30 */
@@ -116,7 +116,8 @@ csp_status csp_reserve(csp_lattice *lat, int64_t pool_capacity);
  * one persistent GPU kernel until a vertex of B receives water (F1 found) or no flow is
  * left (infeasible).
  *   A, B       host arrays of vertex ids (duplicates allowed, treated as sets); nA, nB >= 1.
- *   M          the bound, F2 < M; M <= 0 gives F1 = -1; M >= 2^31 is CSP_ERR_INVALID.
+ *   M          the bound, F2 < M; M <= 0 gives F1 = -1; M >= 2^31 - 1 is CSP_ERR_INVALID (the
+ *              label 2^31 - 1 marks a vertex outside the graph of a reconstruction step).
  *   opt        nullable.
  *   out        result (host).
  *   trace      nullable host buffer of 3 * trace_cap int64: rows (Time, active vertices,

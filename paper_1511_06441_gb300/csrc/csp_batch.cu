@@ -349,7 +349,7 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
     const int wbytes = q[0].lat ? q[0].lat->wbytes : 0;
     for (int64_t i = 0; i < n; i++) {
         const csp_query &x = q[i];
-        if (!x.lat || !x.A || !x.B || x.nA < 1 || x.nB < 1 || x.M >= (1ll << 31) || x.M < -(1ll << 31) + 1 ||
+        if (!x.lat || !x.A || !x.B || x.nA < 1 || x.nB < 1 || x.M >= (1ll << 31) - 1 || x.M < -(1ll << 31) + 1 ||
             x.lat->wbytes != wbytes)
             return CSP_ERR_INVALID;
     }

@@ -233,7 +233,7 @@ void fill_desc(QueryDesc &d, const csp_server_query &q, long long pos)
 
 bool valid_query(const csp_server *s, const csp_server_query &q)
 {
-    if (!q.A || q.nA < 1 || q.nA > kMaxInline || q.M >= (1ll << 31) || q.M < -(1ll << 31) + 1) return false;
+    if (!q.A || q.nA < 1 || q.nA > kMaxInline || q.M >= (1ll << 31) - 1 || q.M < -(1ll << 31) + 1) return false;
     if (q.B) {
         if (q.nB < 1 || q.nB > kMaxInline) return false;
     } else if (q.b_axis < 0 || q.b_axis >= s->lat->d || q.b_coord < 0 || q.b_coord >= s->lat->ext[q.b_axis]) {

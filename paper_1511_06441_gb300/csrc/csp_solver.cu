@@ -614,7 +614,7 @@ csp_status csp_reserve(csp_lattice *L, int64_t pool_capacity)
 csp_status csp_solve_async(csp_lattice *L, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB,
                            int64_t M, const csp_options *opt, int64_t *result_dev, int64_t *trace_dev, int64_t trace_cap)
 {
-    if (!L || !A_dev || !B_dev || nA < 1 || nB < 1 || !result_dev || M >= (1ll << 31) || M < -(1ll << 31) + 1)
+    if (!L || !A_dev || !B_dev || nA < 1 || nB < 1 || !result_dev || M >= (1ll << 31) - 1 || M < -(1ll << 31) + 1)
         return CSP_ERR_INVALID;
     if (trace_dev && trace_cap < 1) return CSP_ERR_INVALID;
     if (!L->ws) return CSP_ERR_INVALID;  // csp_reserve first
@@ -637,7 +637,7 @@ static csp_status solve_host(csp_lattice *L, const int64_t *A, int64_t nA, const
                       const csp_options *opt, csp_result *out, int64_t *trace, int64_t trace_cap, int64_t *trace_len,
                       const int64_t *R, int64_t nR, const ReconLog *rl)
 {
-    if (!L || !out || M >= (1ll << 31) || M < -(1ll << 31) + 1) return CSP_ERR_INVALID;
+    if (!L || !out || M >= (1ll << 31) - 1 || M < -(1ll << 31) + 1) return CSP_ERR_INVALID;
     if (trace && trace_cap < 0) return CSP_ERR_INVALID;
     if (nR < 0 || (nR > 0 && !R)) return CSP_ERR_INVALID;
     csp_status st = check_sets_host(L, A, nA, B, nB);
@@ -908,7 +908,7 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
                                        int64_t nB, int64_t M, int64_t max_cycles, void *stream, int64_t *result_dev)
 {
     if (!extents || !f1_dev || !f2_dev || !A_dev || !B_dev || !result_dev || d < 1 || d > 4 ||
-        (weight_bytes != 1 && weight_bytes != 2) || nA < 1 || nB < 1 || M >= (1ll << 31) || M < -(1ll << 31) + 1)
+        (weight_bytes != 1 && weight_bytes != 2) || nA < 1 || nB < 1 || M >= (1ll << 31) - 1 || M < -(1ll << 31) + 1)
         return CSP_ERR_INVALID;
     int64_t V = 1, ext[4] = {1, 1, 1, 1};
     int stride[4] = {0, 0, 0, 0};

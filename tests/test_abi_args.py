@@ -70,7 +70,7 @@ def test_null_lattice_is_rejected_everywhere(lib):
 def test_static_entry_point_rejects_bad_shapes(lib):
     ext = np.array([4, 4], np.int64)
     A = np.array([0], np.int64)
-    for d, wb, M in [(0, 1, 10), (5, 1, 10), (2, 3, 10), (2, 1, 1 << 31)]:
+    for d, wb, M in [(0, 1, 10), (5, 1, 10), (2, 3, 10), (2, 1, 1 << 31), (2, 1, (1 << 31) - 1)]:
         assert lib.csp_solve_static(d, _p(ext), vp(1), vp(1), wb, vp(1), i64(1), vp(1), i64(1), i64(M), i64(0),
                                     None, vp(1)) == INVALID
     big = np.array([1 << 28, 1], np.int64)  # too many vertices

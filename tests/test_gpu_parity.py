@@ -153,12 +153,13 @@ def test_f2_zero_first_passage_at_size(csp, ext):
     B = np.setdiff1d(synth.face(ext, 1, ext[1] - 1), A)
     F1, X, tau, rows = brute.dijkstra_trace(ext, f1, A, B)
     lat = csp.Lattice(ext, f1, f2)
-    got = lat.solve(A, B, 2**31 - 1, trace=True, trace_cap=1 << 15)
+    M = 2**31 - 2  # the largest bound the solver accepts (2^31 - 1 marks removed vertices)
+    got = lat.solve(A, B, M, trace=True, trace_cap=1 << 15)
     assert (got.F1, got.X, got.F2) == (F1, X, 0)
     np.testing.assert_array_equal(got.trace, rows)
     lab = lat.labels()
     reached = np.isfinite(tau) & (tau <= F1)
-    assert (lab[reached] == 2**31 - 1).all() and (lab[~reached] == 0).all()
+    assert (lab[reached] == M).all() and (lab[~reached] == 0).all()
     lat.close()
 
 

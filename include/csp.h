@@ -38,7 +38,7 @@ typedef enum {
     CSP_ERR_OOM = 2,      /* device or host allocation failed */
     CSP_ERR_CUDA = 3,     /* a CUDA call failed; csp_last_error() has the text */
     CSP_ERR_CAPACITY = 4, /* the flow pool overflowed, or arrival times would reach 2^30 */
-    CSP_ERR_TIMEOUT = 5,  /* max_cycles reached */
+    CSP_ERR_TIMEOUT = 5,  /* max_cycles reached, or the solve ran past its time limit (csp_options) */
     CSP_ERR_BARRIER = 6   /* a device-side barrier wait gave up after its time limit */
 } csp_status;
 
@@ -107,8 +107,9 @@ void csp_destroy_lattice(csp_lattice *lat);
 /* Number of vertices of the lattice. */
 int64_t csp_num_vertices(const csp_lattice *lat);
 
-/* Allocates the solver workspace now (labels, offers, triggered list, two flow-pool
- * buffers of pool_capacity flows; 0 = automatic), so that later solves allocate nothing. */
+/* Allocates the solver workspace now (labels, offers, arrival lists, two flow-pool
+ * buffers of pool_capacity slots; 0 = automatic), so that later solves allocate nothing
+ * (unless a csp_solve must grow the pool or a longer trace is requested). */
 csp_status csp_reserve(csp_lattice *lat, int64_t pool_capacity);
 
 /*
@@ -163,11 +164,13 @@ csp_status csp_solve_async(csp_lattice *lat, const int64_t *A_dev, int64_t nA, c
  *   M, max_cycles    as for csp_solve (max_cycles 0 = no limit).
  *   stream           cudaStream_t or NULL.
  *   result_dev       device record of 16 int64, laid out as for csp_solve_async.
- * Enqueues the solve and returns without waiting.  The layout needs 28.125 + 8d bytes per
- * vertex (labels, offers, B bitmap, arrival list, a 16-byte edge record; 16 more for
- * 16-bit weights with d >= 3) plus 24 bytes per flow-pool slot (two buffers); whatever the vertex arrays leave of the static array becomes the flow pool.  A lattice whose vertex arrays do not fit is
- * rejected with CSP_ERR_INVALID (csp_last_error() says so); a solve whose flows do not fit
- * reports CSP_ERR_CAPACITY in result_dev[0].  No trace is recorded.  The first call on a
+ * Enqueues the solve and returns without waiting.  The layout needs 28.125 bytes per vertex
+ * (labels, offers, B bitmap, a 16-byte edge record; 16 more for 16-bit weights with
+ * d >= 3), 28 bytes per flow-pool slot (two pool buffers and an arrival-list entry) and
+ * 8 KiB of arrival list per CTA; whatever the vertex arrays leave of the static array
+ * becomes the flow pool.  A lattice whose vertex arrays do not fit is rejected with
+ * CSP_ERR_INVALID (csp_last_error() says so); a solve whose flows do not fit reports
+ * CSP_ERR_CAPACITY in result_dev[0].  No trace is recorded.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) for that device;
  * make that first call before capturing any stream.  All calls share the array and
  * each call overwrites what the previous one left, so calls that may overlap on the GPU

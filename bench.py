@@ -324,6 +324,8 @@ def run_ours(args):
         line["anticorrelated"] = bench_anticorrelated(csp, synth)
     if world == 1 and args.open_problems:
         line["open_problems"] = bench_open_problems(csp, synth)
+    if world == 1 and args.fractal:
+        line["fractal"] = bench_fractal(csp, synth)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, ORACLE_SAMPLE_CYCLES)
     print(json.dumps(line), flush=True)
@@ -419,6 +421,32 @@ def bench_open_problems(csp, synth, seeds=(6, 7, 8, 9), side=1024):
                              "mean_phantoms_per_solve": float(np.mean(ph)),
                              "phantoms_per_launched_flow": float(np.sum(ph)) / max(1, float(np.sum(la)))})
     return out
+
+
+def bench_fractal(csp, synth, t=4096):
+    """The environments omega_1 .. omega_k (t = 2^k) of the proof of the paper's t log t lower
+    bound on the active set: N_t(omega_j), the active vertices at time t (all of V has
+    |x| <= t), against the proof's N_t(omega_1) + (j - 1) 4t/15."""
+    import torch
+    k = t.bit_length() - 1
+    rows = []
+    for j in range(1, k + 1):
+        inst = synth.fractal_environment(t, j)
+        lat = csp.Lattice(inst.extents, inst.f1, inst.f2)
+        lat.solve(inst.A, inst.B, inst.M, trace=True, trace_cap=t + 8)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = lat.solve(inst.A, inst.B, inst.M, trace=True, trace_cap=t + 8)
+        sec = time.perf_counter() - t0
+        lat.close()
+        row = r.trace[int(np.searchsorted(r.trace[:, 0], t))]
+        assert int(row[0]) == t
+        rows.append({"j": j, "N_t": int(row[1]), "N_t_per_t": int(row[1]) / t, "live_flows": int(row[2]),
+                     "F1": r.F1, "solve_ms": 1e3 * sec})
+    n1 = rows[0]["N_t"]
+    for x in rows:
+        x["proof_N_t"] = n1 + (x["j"] - 1) * 4 * t / 15
+    return {"workload": f"lattice2d_fractal_t{t}", "extents": [2 * t + 1, t + 2], "t": t, "rows": rows}
 
 
 def bench_batched(csp, synth):
@@ -546,6 +574,8 @@ def main():
     ap.add_argument("--batch", type=int, default=1, help="also measure 512 batched instances vs one launch each (N=1)")
     ap.add_argument("--open-problems", type=int, default=0,
                     help="also measure the mean active-set size vs time on 1024^2 i.i.d. lattices (N=1)")
+    ap.add_argument("--fractal", type=int, default=0,
+                    help="also count the active vertices at time t = 4096 on the environments omega_j (N=1)")
     ap.add_argument("--anticorrelated", type=int, default=1,
                     help="also time the 4096^2 anti-correlated solve and its path (N=1; ~1.5 min)")
     ap.add_argument("--serve", type=int, default=2000,

@@ -548,7 +548,7 @@ __device__ __forceinline__ void put_flow(const Params<W> &P, int ob, Counters *C
 //           CTA's region; the launch phase finds, for each improved vertex, the one
 //           candidate that won;
 //   survives otherwise: copied to the output pool.
-// Pool chunks (one tile each) arrive by bulk copies into two shared-memory stages; the
+// Pool chunks (one tile each) arrive by bulk copies into NSTAGE shared-memory stages; the
 // warps work through their slices of a tile independently (no block barrier in the
 // loop): the last warp to finish reading a stage starts the copy of the tile after next
 // into it, and each warp compacts its survivors and arrivals with ballots and claims

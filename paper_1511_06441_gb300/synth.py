@@ -233,6 +233,69 @@ def workload_point_source(side: int = 1024, seed: int = 6) -> Instance:
     return Instance(ext, f1, f2, np.array([c], np.int64), B, 0, f"lattice2d_{side}_U16_point_source")
 
 
+FRACTAL_M = 2**31 - 2   # a bound no path reaches: the weights are all 0
+
+
+def fractal_environment(t: int, levels: int) -> Instance:
+    """The environment omega_j, j = ``levels``, of the proof of the paper's t log t lower
+    bound on the active set (Section "Large sets of active vertices", Theorem 3), on
+    V = [-t, t] x [0, t + 1] of Z^2.
+
+    Travel times are 1 on the y axis and on the construction's segments and 2 elsewhere;
+    weights are 0 and M is never reached, so the problem is first-passage percolation.
+    Water starts on the whole x axis (A = the row y = 0); B = the row y = t + 1, which
+    the y axis reaches at time t + 1, so a solve passes Time t.
+
+    Construction on the left half (the right half is its mirror image in the y axis),
+    t = 2^k: L = (-t/2, 0), O = (0, t/2), T = (0, t).  omega_1: the y axis and the
+    segment LO are fast, and the triangles are {LOT}.  omega_{j+1}: in every triangle
+    (L, O, T), where O = L + (s, s) and T = L + (s, 2s), the segments L0 X (L0 the midpoint
+    of LO, X the midpoint of LT: vertical) and X T0 (T0 the midpoint of OT: slope 1)
+    become fast, and the triangles become the halves (L, L0, X) and (X, T0, T).  A slope-1
+    segment from P to P + (m, m) is the staircase P + (i, i) -> P + (i, i + 1) ->
+    P + (i + 1, i + 1), i < m, whose corners lie on the triangle's side of the segment.
+    Vertex ids: x + t fastest, then y.
+    """
+    k = int(t).bit_length() - 1
+    if t < 2 or t != 1 << k or not 1 <= levels <= k:
+        raise ValueError("t must be a power of two >= 2 and 1 <= levels <= log2(t)")
+    W, H = 2 * t + 1, t + 2
+    fast_h = np.zeros((H, W), bool)   # edge (x, y) -> (x + 1, y), at [y, x + t]
+    fast_v = np.zeros((H, W), bool)   # edge (x, y) -> (x, y + 1), at [y, x + t]
+
+    def vertical(x, y0, y1):          # (x, y) -> (x, y + 1) for y0 <= y < y1, and its mirror
+        fast_v[y0:y1, t + x] = True
+        fast_v[y0:y1, t - x] = True
+
+    def staircase(px, py, m):
+        i = np.arange(m)
+        fast_v[py + i, t + px + i] = True
+        fast_v[py + i, t - px - i] = True
+        fast_h[py + i + 1, t + px + i] = True           # (px+i, .) -> (px+i+1, .)
+        fast_h[py + i + 1, t - px - i - 1] = True       # its mirror (-px-i-1, .) -> (-px-i, .)
+
+    vertical(0, 0, H - 1)
+    staircase(-t // 2, 0, t // 2)
+    triangles = [(-t // 2, 0, t // 2)]                  # (L_x, L_y, s)
+    for _ in range(levels - 1):
+        halves = []
+        for lx, ly, s in triangles:
+            h = s // 2
+            vertical(lx + h, ly + h, ly + s)            # L0 = L + (h, h) up to X = L + (h, s)
+            staircase(lx + h, ly + s, h)                # X up to T0 = L + (s, s + h)
+            halves += [(lx, ly, h), (lx + h, ly + s, h)]
+        triangles = halves
+    ext = [W, H]
+    V = W * H
+    f1 = np.stack([np.where(fast_h, 1, 2).reshape(V), np.where(fast_v, 1, 2).reshape(V)])
+    f1[upper_face_mask(ext)] = 0
+    f1 = f1.astype(np.uint8)
+    f2 = np.zeros_like(f1)
+    A = face(ext, 1, 0)
+    B = face(ext, 1, H - 1)
+    return Instance(ext, f1, f2, A, B, FRACTAL_M, f"lattice2d_fractal_t{t}_omega{levels}")
+
+
 def anticorrelated_weights(extents: Sequence[int], seed: int = 3):
     """f1 = min(255, Geometric(0.1)), f2 = 256 - f1, stored as uint16; upper faces zeroed."""
     d, V = len(extents), num_vertices(extents)

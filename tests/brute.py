@@ -14,7 +14,8 @@ its definition in the paper:
 * :func:`phantoms` - the flows started on an edge that already carries one, from the same
   label histories (the paper's phantom edges, Step 5).
 * :func:`dijkstra_trace` - for f2 = 0 the problem is first-passage percolation: F1 is the
-  Dijkstra distance tau (computed by scipy) and the state at time T is {tau <= T}.
+  Dijkstra distance tau (computed by scipy) and the state at time T is {tau <= T};
+  :func:`first_passage_row` gives one row of that trace.
 """
 from __future__ import annotations
 
@@ -216,22 +217,10 @@ def tau(extents, f1, A) -> np.ndarray:
     return dijkstra(G, directed=True, indices=np.asarray(A, dtype=np.int64), min_only=True)
 
 
-def dijkstra_trace(extents, f1, A, B):
-    """For f2 = 0: (F1, X, x candidates, trace) from first-passage times.
-
-    F1 = min tau over B; X = smallest id attaining it; the cycle times are the distinct
-    tau values in (0, F1]; at the end of cycle T a directed edge (v, u) carries a live flow
-    iff tau(v) <= T < tau(u), and v is active iff it has such an edge.
-    """
-    ext = [int(n) for n in extents]
+def _edge_pairs(ext, f1):
+    """(src, dst) of every directed edge present (f1 > 0), from coordinates."""
     d = len(ext)
     V = int(np.prod(ext))
-    t = tau(ext, f1, A)
-    Bv = np.asarray(B, dtype=np.int64)
-    tb = t[Bv]
-    F1 = np.min(tb)
-    if not np.isfinite(F1):
-        F1 = None
     f1a = np.asarray(f1).reshape(d, V)
     v = np.arange(V)
     strides = np.cumprod([1] + ext[:-1])
@@ -241,8 +230,32 @@ def dijkstra_trace(extents, f1, A, B):
         ok = (ck + 1 < ext[k]) & (f1a[k] > 0)
         pairs.append((v[ok], v[ok] + strides[k]))
         pairs.append((v[ok] + strides[k], v[ok]))
-    src = np.concatenate([p[0] for p in pairs])
-    dst = np.concatenate([p[1] for p in pairs])
+    return np.concatenate([p[0] for p in pairs]), np.concatenate([p[1] for p in pairs])
+
+
+def first_passage_row(extents, f1, t, T):
+    """Trace row (T, active vertices, live flows) at the end of cycle T for f2 = 0, from the
+    first-passage times t: a directed edge (v, u) carries a live flow iff
+    t(v) <= T < t(u), and v is active iff it has such an edge."""
+    src, dst = _edge_pairs([int(n) for n in extents], f1)
+    live = (t[src] <= T) & (t[dst] > T)
+    return (int(T), len(np.unique(src[live])), int(live.sum()))
+
+
+def dijkstra_trace(extents, f1, A, B):
+    """For f2 = 0: (F1, X, x candidates, trace) from first-passage times.
+
+    F1 = min tau over B; X = smallest id attaining it; the cycle times are the distinct
+    tau values in (0, F1]; the row of cycle T is :func:`first_passage_row`.
+    """
+    ext = [int(n) for n in extents]
+    t = tau(ext, f1, A)
+    Bv = np.asarray(B, dtype=np.int64)
+    tb = t[Bv]
+    F1 = np.min(tb)
+    if not np.isfinite(F1):
+        F1 = None
+    src, dst = _edge_pairs(ext, f1)
     finite = t[np.isfinite(t)]
     times = np.unique(finite[finite > 0])
     if F1 is not None:

@@ -9,7 +9,9 @@ The solvers live in ``csp_oracle.c`` (plain C, compiled here with gcc on first u
 * :func:`cycle`  - O1, the paper's cycle loop (Algorithm 1, Steps 1-9), with trace;
 * :func:`pareto` - O2, an independent Dijkstra over (vertex, quality) states;
 * :func:`lexmin` - unconstrained lexicographic (F1, F2) Dijkstra (the bound M of the
-  anti-correlated workload, and its answer where that bound does not bind).
+  anti-correlated workload, and its answer where that bound does not bind);
+* :func:`cycle_graph`, :func:`pareto_graph`, :func:`reconstruct_graph` - O1, O2 and the
+  repeated application on a general graph given by adjacency slots.
 
 Parity unpinned: nothing.  Every output is pinned by the tests against brute force,
 plain Dijkstra, closed forms or the paper's Lemma; see the C file's header.
@@ -58,7 +60,10 @@ def _load():
                                           ctypes.c_int64, ctypes.c_int64, i64p]
             lib.oracle_lexmin.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
                                           ctypes.c_int64, i64p, i64p, ctypes.c_int64, i64p]
-            for f in (lib.oracle_cycle, lib.oracle_pareto, lib.oracle_lexmin):
+            lib.oracle_cycle_graph.argtypes = [ctypes.c_int64, ctypes.c_int, i64p] + lib.oracle_cycle.argtypes[2:]
+            lib.oracle_pareto_graph.argtypes = [ctypes.c_int64, ctypes.c_int, i64p] + lib.oracle_pareto.argtypes[2:]
+            for f in (lib.oracle_cycle, lib.oracle_pareto, lib.oracle_lexmin, lib.oracle_cycle_graph,
+                      lib.oracle_pareto_graph):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -114,9 +119,33 @@ def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 <
     With ``allow_timeout`` a run stopped by ``max_cycles`` returns its work counts
     (``cycles``, ``updates``, ``launched``) with ``F1 = -2`` instead of raising.
     """
-    lib = _load()
     ext, f1, f2, A, B = _common(extents, f1, f2, A, B)
     V = int(np.prod(ext))
+    return _cycle(lambda *rest: _load().oracle_cycle(len(ext), _p64(ext), _p32(f1), _p32(f2), *rest), V, A, B, M,
+                  max_cycles, trace, labels, snap_time, allow_timeout, removed)
+
+
+def _graph_arrays(nbr, f1, f2):
+    nbr = np.ascontiguousarray(np.asarray(nbr, dtype=np.int64))
+    V, S = nbr.shape
+    f1 = np.ascontiguousarray(np.asarray(f1).astype(np.int32).reshape(V, S))
+    f2 = np.ascontiguousarray(np.asarray(f2).astype(np.int32).reshape(V, S))
+    return nbr, f1, f2, V, S
+
+
+def cycle_graph(nbr, f1, f2, A, B, M: int, *, max_cycles: int = 1 << 62, trace: bool = True,
+                labels: bool = False, snap_time: Optional[int] = None, allow_timeout: bool = False,
+                removed=None) -> Result:
+    """O1 on a general graph: ``nbr`` (V, S) neighbour ids (-1: empty slot), ``f1``/``f2``
+    (V, S) the edge in each slot; x_dir is the slot of x at x_src."""
+    nbr, f1, f2, V, S = _graph_arrays(nbr, f1, f2)
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
+    return _cycle(lambda *rest: _load().oracle_cycle_graph(V, S, _p64(nbr), _p32(f1), _p32(f2), *rest), V, A, B,
+                  M, max_cycles, trace, labels, snap_time, allow_timeout, removed)
+
+
+def _cycle(call, V, A, B, M, max_cycles, trace, labels, snap_time, allow_timeout, removed) -> Result:
     rem = None
     if removed is not None:
         rem = np.zeros(V, np.uint8)
@@ -129,12 +158,10 @@ def cycle(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 <
         snap = np.zeros(V, np.int64) if snap_time is not None else None
         sl = np.zeros(1, np.int64)
         lab = np.zeros(V, np.int64) if labels else None
-        rc = lib.oracle_cycle(len(ext), _p64(ext), _p32(f1), _p32(f2), _p64(A), A.size, _p64(B), B.size,
-                              int(M), int(max_cycles), _p64(res), _p64(tr), cap if trace else 0, _p64(tl),
-                              -1 if snap_time is None else int(snap_time),
-                              _p64(snap) if snap is not None else None, _p64(sl),
-                              _p64(lab) if lab is not None else None,
-                              rem.ctypes.data if rem is not None else None)
+        rc = call(_p64(A), A.size, _p64(B), B.size, int(M), int(max_cycles), _p64(res), _p64(tr),
+                  cap if trace else 0, _p64(tl), -1 if snap_time is None else int(snap_time),
+                  _p64(snap) if snap is not None else None, _p64(sl), _p64(lab) if lab is not None else None,
+                  rem.ctypes.data if rem is not None else None)
         if rc == TIMEOUT and allow_timeout:
             res[:5] = -2
         elif rc != OK:
@@ -164,7 +191,12 @@ def reconstruct(extents: Sequence[int], f1, f2, A, B, M: int, first: Optional[Re
     B' = {Y}, M' = F2 - f2(x) + 1, V' = V minus (B and the path vertices found so far),
     A' = A, until Y is in A.  Returns (path from A to X, per-step results), or
     (None, [first]) when infeasible.  Each step is a full O1 solve."""
-    r = first if first is not None else cycle(extents, f1, f2, A, B, M, trace=False)
+    return _reconstruct(lambda **kw: cycle(extents, f1, f2, **kw),
+                        lambda y, d: edge_weight(extents, f1, f2, y, d)[1], A, B, M, first, max_steps)
+
+
+def _reconstruct(solve, weight_of_x, A, B, M, first, max_steps):
+    r = first if first is not None else solve(A=A, B=B, M=M, trace=False)
     steps = [r]
     if r.F1 < 0:
         return None, steps
@@ -173,9 +205,9 @@ def reconstruct(extents: Sequence[int], f1, f2, A, B, M: int, first: Optional[Re
     path = [r.X]
     F2, Y, xd, X = r.F2, r.x_src, r.x_dir, r.X
     while Y not in Aset and len(steps) <= max_steps:
-        _, w2 = edge_weight(extents, f1, f2, Y, xd)
+        w2 = weight_of_x(Y, xd)
         removed = sorted(Bset | set(path))
-        r = cycle(extents, f1, f2, A, [Y], F2 - w2 + 1, trace=False, removed=removed)
+        r = solve(A=A, B=[Y], M=F2 - w2 + 1, trace=False, removed=removed)
         steps.append(r)
         if r.F1 < 0 or r.X != Y:
             raise RuntimeError("repeated application lost the path")
@@ -198,6 +230,29 @@ def pareto(extents: Sequence[int], f1, f2, A, B, M: int) -> Result:
     r.updates = int(res[6])
     r.launched = int(res[7])
     return r
+
+
+def pareto_graph(nbr, f1, f2, A, B, M: int) -> Result:
+    """O2 on a general graph (arrays as in :func:`cycle_graph`)."""
+    nbr, f1, f2, V, S = _graph_arrays(nbr, f1, f2)
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
+    res = np.zeros(8, np.int64)
+    rc = _load().oracle_pareto_graph(V, S, _p64(nbr), _p32(f1), _p32(f2), _p64(A), A.size, _p64(B), B.size,
+                                     int(M), _p64(res))
+    if rc != OK:
+        raise OracleError(rc)
+    r = Result(*[int(x) for x in res[:5]])
+    r.updates = int(res[6])
+    r.launched = int(res[7])
+    return r
+
+
+def reconstruct_graph(nbr, f1, f2, A, B, M: int, first: Optional[Result] = None, max_steps: int = 1 << 30):
+    """:func:`reconstruct` on a general graph: f2(x) is the weight in slot x_dir of x_src."""
+    f2a = np.asarray(f2).reshape(np.asarray(nbr).shape)
+    return _reconstruct(lambda **kw: cycle_graph(nbr, f1, f2, **kw), lambda y, d: int(f2a[y, d]), A, B, M, first,
+                        max_steps)
 
 
 def lexmin(extents: Sequence[int], f1, f2, A, B, *, full: bool = False, path: bool = False):

@@ -25,6 +25,11 @@
  * they are read only where c_k + 1 < n_k, and f1 <= 0 means the edge is absent.
  * Direction dir = 2k + s leads from v to v + e_k (s = 0) or v - e_k (s = 1).
  *
+ * Graph (oracle_cycle_graph, oracle_pareto_graph; Section 1 states the method for any
+ * graph): V vertices with S adjacency slots each; slot j of v holds the neighbour
+ * nbr[v*S+j] (-1: empty) and the edge's f1[v*S+j] >= 1, f2[v*S+j].  The direction of an
+ * edge is its slot at the vertex it leaves.
+ *
  * Readings of the paper adopted here (where it is silent or inconsistent):
  *   - the bound is strict, F2 < M (Section 1), matching "quality 0 cannot travel";
  *   - labels only increase: an arrival of better water raises the label of an active
@@ -57,8 +62,10 @@ enum { OR_OK = 0, OR_INVALID = 1, OR_OOM = 2, OR_TIMEOUT = 5 };
 
 typedef struct {
     int d;
+    int slots;                    /* directions per vertex: 2d on a lattice, S on a graph */
     int64_t ext[4], stride[4], V;
     const int32_t *f1, *f2;
+    const int64_t *nbr;           /* graph only: nbr[v * S + j] = neighbour in slot j, or -1 */
     const unsigned char *removed; /* nullable: vertices not in the graph (V' of Section 1) */
 } lattice_t;
 
@@ -73,8 +80,29 @@ static int lattice_init(lattice_t *L, int d, const int64_t *ext, const int32_t *
         L->stride[k] = L->V;
         L->V *= ext[k];
     }
+    L->slots = 2 * d;
     L->f1 = f1;
     L->f2 = f2;
+    L->nbr = NULL;
+    L->removed = NULL;
+    return OR_OK;
+}
+
+/* A general graph (Section 1 allows any graph; the lattice is the bounded-degree case
+ * the paper implements): vertex v has S slots, slot j holding the neighbour nbr[v*S+j]
+ * (-1: empty) and the edge's f1[v*S+j] >= 1 and f2[v*S+j].  An undirected edge appears
+ * in a slot of each end; the oracle itself also accepts one-way edges. */
+static int graph_init(lattice_t *L, int64_t V, int S, const int64_t *nbr, const int32_t *f1, const int32_t *f2)
+{
+    if (V < 1 || S < 1) return OR_INVALID;
+    for (int64_t i = 0; i < V * S; i++)
+        if (nbr[i] < -1 || nbr[i] >= V || (nbr[i] >= 0 && f1[i] < 1)) return OR_INVALID;
+    L->d = 0;
+    L->slots = S;
+    L->V = V;
+    L->f1 = f1;
+    L->f2 = f2;
+    L->nbr = nbr;
     L->removed = NULL;
     return OR_OK;
 }
@@ -83,6 +111,14 @@ static int lattice_init(lattice_t *L, int d, const int64_t *ext, const int32_t *
  * *time and *weight receive f1 and f2 of the edge. */
 static int64_t neighbour(const lattice_t *L, int64_t v, int dir, int64_t *time, int64_t *weight)
 {
+    if (L->nbr) {
+        const int64_t i = v * L->slots + dir, u = L->nbr[i];
+        if (u < 0) return -1;
+        if (L->removed && (L->removed[u] || L->removed[v])) return -1;
+        *time = L->f1[i];
+        *weight = L->f2[i];
+        return u;
+    }
     int k = dir / 2, s = dir % 2;
     int64_t ck = (v / L->stride[k]) % L->ext[k];
     int64_t u, slot;
@@ -153,12 +189,12 @@ static int flows_push(flows_t *F, flow_t f)
 
 /* Start a flow on every edge (v, u) along which water of quality Label(v) would still
  * raise Label(u): Label(v) - f2 > Label(u) (Step 4, TriggerEdges; Step 5 creates the
- * flow, a phantom if the edge already carries water).  on_edge[v * 2d + dir] counts the
+ * flow, a phantom if the edge already carries water).  on_edge[v * slots + dir] counts the
  * flows on each directed edge; a flow started while it is positive is a phantom. */
 static int launch_from(const lattice_t *L, const int64_t *label, int64_t v, flows_t *F, int64_t *launched,
                        int64_t *on_edge, int64_t *phantoms)
 {
-    for (int dir = 0; dir < 2 * L->d; dir++) {
+    for (int dir = 0; dir < L->slots; dir++) {
         int64_t t, w;
         int64_t u = neighbour(L, v, dir, &t, &w);
         if (u < 0) continue;
@@ -166,7 +202,7 @@ static int launch_from(const lattice_t *L, const int64_t *label, int64_t v, flow
             flow_t f = {v, dir, u, label[v], w, t};
             if (flows_push(F, f)) return OR_OOM;
             (*launched)++;
-            int64_t *c = &on_edge[v * 2 * L->d + dir];
+            int64_t *c = &on_edge[v * L->slots + dir];
             if (*c > 0) (*phantoms)++;
             (*c)++;
         }
@@ -218,16 +254,13 @@ static int cmp_i64(const void *x, const void *y)
  * labels_out (nullable, V entries) receives the labels at termination.  removed
  * (nullable, V bytes) lists vertices that are not part of the graph; A and B must avoid them.
  */
-int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2,
-                 const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
-                 int64_t max_cycles, int64_t *res,
-                 int64_t *trace, int64_t trace_cap, int64_t *trace_len,
-                 int64_t snap_time, int64_t *snap, int64_t *snap_len, int64_t *labels_out,
-                 const unsigned char *removed)
+static int cycle_core(lattice_t L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                      int64_t max_cycles, int64_t *res,
+                      int64_t *trace, int64_t trace_cap, int64_t *trace_len,
+                      int64_t snap_time, int64_t *snap, int64_t *snap_len, int64_t *labels_out,
+                      const unsigned char *removed)
 {
-    lattice_t L;
-    int rc = lattice_init(&L, d, ext, f1, f2);
-    if (rc) return rc;
+    int rc = OR_OK;
     L.removed = removed;
     const int64_t V = L.V;
     unsigned char *inA = calloc((size_t)V, 1), *inB = calloc((size_t)V, 1);
@@ -238,7 +271,7 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
     int64_t *touched = malloc((size_t)V * sizeof(int64_t));
     int64_t *improved = malloc((size_t)V * sizeof(int64_t));
     int64_t *xsrc = malloc((size_t)V * sizeof(int64_t)), *xdir = malloc((size_t)V * sizeof(int64_t));
-    int64_t *on_edge = calloc((size_t)V * 2 * d, sizeof(int64_t));
+    int64_t *on_edge = calloc((size_t)V * L.slots, sizeof(int64_t));
     flows_t F = {0, 0, 0};
     int64_t rows = 0, Time = 0, cycles = 0, updates = 0, launched = 0, phantoms = 0;
     if (!inA || !inB || !label || !stamp || !bq || !bsrc || !bdir || !touched || !improved || !xsrc || !xdir ||
@@ -266,7 +299,7 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
         if (inA[v]) label[v] = M;
     for (int64_t v = 0; v < V; v++)
         if (inA[v] && (rc = launch_from(&L, label, v, &F, &launched, on_edge, &phantoms))) goto done;
-    prune(&F, label, on_edge, 2 * d);
+    prune(&F, label, on_edge, L.slots);
     {
         int64_t act = count_active(&F, stamp, 0, NULL);
         if (rows < trace_cap) {
@@ -301,7 +334,7 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
                 F.a[j++] = *f;
                 continue;
             }
-            on_edge[f->src * 2 * d + f->dir]--;  /* arrived: off the edge */
+            on_edge[f->src * L.slots + f->dir]--;  /* arrived: off the edge */
             int64_t q = f->Q - f->f2, u = f->dst;
             if (bq[u] == INT64_MIN) touched[nt++] = u;
             if (q > bq[u] || (q == bq[u] && (f->src < bsrc[u] || (f->src == bsrc[u] && f->dir < bdir[u])))) {
@@ -328,7 +361,7 @@ int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2
         for (int64_t i = 0; i < ni; i++)
             if ((rc = launch_from(&L, label, improved[i], &F, &launched, on_edge, &phantoms))) goto done;
         /* Steps 7-9. */
-        prune(&F, label, on_edge, 2 * d);
+        prune(&F, label, on_edge, L.slots);
         int64_t act = count_active(&F, stamp, cycles, NULL);
         if (rows < trace_cap) {
             trace[3 * rows] = Time;
@@ -364,6 +397,34 @@ done:
     free(inA); free(inB); free(label); free(stamp); free(bq); free(bsrc); free(bdir);
     free(touched); free(improved); free(xsrc); free(xdir); free(F.a); free(on_edge);
     return rc;
+}
+
+int oracle_cycle(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2,
+                 const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                 int64_t max_cycles, int64_t *res,
+                 int64_t *trace, int64_t trace_cap, int64_t *trace_len,
+                 int64_t snap_time, int64_t *snap, int64_t *snap_len, int64_t *labels_out,
+                 const unsigned char *removed)
+{
+    lattice_t L;
+    int rc = lattice_init(&L, d, ext, f1, f2);
+    if (rc) return rc;
+    return cycle_core(L, A, nA, B, nB, M, max_cycles, res, trace, trace_cap, trace_len, snap_time, snap, snap_len, labels_out, removed);
+}
+
+/* O1 on a general graph (see graph_init); the same outputs, x_dir being the slot of x in
+ * the adjacency of x_src. */
+int oracle_cycle_graph(int64_t V, int S, const int64_t *nbr, const int32_t *f1, const int32_t *f2,
+                       const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                       int64_t max_cycles, int64_t *res,
+                       int64_t *trace, int64_t trace_cap, int64_t *trace_len,
+                       int64_t snap_time, int64_t *snap, int64_t *snap_len, int64_t *labels_out,
+                       const unsigned char *removed)
+{
+    lattice_t L;
+    int rc = graph_init(&L, V, S, nbr, f1, f2);
+    if (rc) return rc;
+    return cycle_core(L, A, nA, B, nB, M, max_cycles, res, trace, trace_cap, trace_len, snap_time, snap, snap_len, labels_out, removed);
 }
 
 /* ------------------------------------------------------------------ O2 */
@@ -432,12 +493,10 @@ static state_t heap_pop(heap_t *H)
  * lighter).  The first settled vertex of B gives F1, X, x and F2 = M - q.
  * res[0..7] = F1, X, x_src, x_dir, F2, -1, states_settled, states_pushed.
  */
-int oracle_pareto(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2,
-                  const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M, int64_t *res)
+static int pareto_core(lattice_t L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                       int64_t *res)
 {
-    lattice_t L;
-    int rc = lattice_init(&L, d, ext, f1, f2);
-    if (rc) return rc;
+    int rc = OR_OK;
     const int64_t V = L.V;
     unsigned char *inA = calloc((size_t)V, 1), *inB = calloc((size_t)V, 1);
     int64_t *best = calloc((size_t)V, sizeof(int64_t)); /* best settled quality, 0 = none */
@@ -469,7 +528,7 @@ int oracle_pareto(int d, const int64_t *ext, const int32_t *f1, const int32_t *f
             res[4] = M - s.q;
             break;
         }
-        for (int dir = 0; dir < 2 * d; dir++) {
+        for (int dir = 0; dir < L.slots; dir++) {
             int64_t t, w;
             int64_t u = neighbour(&L, s.v, dir, &t, &w);
             if (u < 0 || s.q - w <= best[u]) continue;
@@ -483,6 +542,25 @@ int oracle_pareto(int d, const int64_t *ext, const int32_t *f1, const int32_t *f
 done:
     free(inA); free(inB); free(best); free(H.a);
     return rc;
+}
+
+int oracle_pareto(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2,
+                  const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M, int64_t *res)
+{
+    lattice_t L;
+    int rc = lattice_init(&L, d, ext, f1, f2);
+    if (rc) return rc;
+    return pareto_core(L, A, nA, B, nB, M, res);
+}
+
+/* O2 on a general graph (see graph_init). */
+int oracle_pareto_graph(int64_t V, int S, const int64_t *nbr, const int32_t *f1, const int32_t *f2,
+                        const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M, int64_t *res)
+{
+    lattice_t L;
+    int rc = graph_init(&L, V, S, nbr, f1, f2);
+    if (rc) return rc;
+    return pareto_core(L, A, nA, B, nB, M, res);
 }
 
 /* ------------------------------------------------------------------ lexicographic Dijkstra */
@@ -546,7 +624,7 @@ int oracle_lexmin(int d, const int64_t *ext, const int32_t *f1, const int32_t *f
             }
             break;
         }
-        for (int dir = 0; dir < 2 * d; dir++) {
+        for (int dir = 0; dir < L.slots; dir++) {
             int64_t t, w;
             int64_t u = neighbour(&L, s.v, dir, &t, &w);
             if (u < 0 || done_v[u]) continue;

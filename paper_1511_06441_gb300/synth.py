@@ -426,3 +426,136 @@ def random_small_instance(seed: int, max_vertices: int = 16, dims=(1, 2, 3), f_l
     B = np.sort(perm[nA:nA + nB]).astype(np.int64)
     M = int(1 + r[15] % np.uint64(25))
     return Instance(ext, f1.astype(np.uint8), f2.astype(np.uint8), A, B, M, f"tiny{seed}")
+
+
+# ---------------------------------------------------------------- general graphs
+
+@dataclasses.dataclass
+class GraphInstance:
+    """One problem on a general graph of bounded degree (Section 1 of the paper states the
+    method for any graph).  Vertex v has S adjacency slots: ``nbr[v, j]`` is the neighbour
+    in slot j (-1: empty), ``f1[v, j]`` >= 1 and ``f2[v, j]`` the travel time and weight of
+    that edge.  Undirected: an edge sits in one slot at each end with the same weights.
+    The direction of an edge (the x_dir of a result) is its slot at the vertex it leaves."""
+    nbr: np.ndarray         # (V, S) int64
+    f1: np.ndarray          # (V, S) uint8 | uint16 (0 in empty slots)
+    f2: np.ndarray          # (V, S) same dtype
+    A: np.ndarray
+    B: np.ndarray
+    M: int
+    name: str = ""
+
+    @property
+    def V(self) -> int:
+        return int(self.nbr.shape[0])
+
+    @property
+    def S(self) -> int:
+        return int(self.nbr.shape[1])
+
+    @property
+    def weight_bytes(self) -> int:
+        return self.f1.dtype.itemsize
+
+
+def graph_from_lattice(extents: Sequence[int], f1, f2):
+    """The lattice as adjacency slots in its direction order (slot 2k: +e_k, 2k+1: -e_k),
+    absent edges as empty slots: (nbr, f1, f2), each (V, 2d)."""
+    d, V = len(extents), num_vertices(extents)
+    st = strides(extents)
+    f1 = np.asarray(f1).reshape(d, V)
+    f2 = np.asarray(f2).reshape(d, V)
+    v = np.arange(V, dtype=np.int64)
+    nbr = np.full((V, 2 * d), -1, np.int64)
+    g1 = np.zeros((V, 2 * d), f1.dtype)
+    g2 = np.zeros((V, 2 * d), f2.dtype)
+    for k in range(d):
+        ok = f1[k] > 0                               # the edge (v, v + e_k) exists
+        up = v[ok] + st[k]
+        nbr[v[ok], 2 * k] = up
+        g1[v[ok], 2 * k] = f1[k][ok]
+        g2[v[ok], 2 * k] = f2[k][ok]
+        nbr[up, 2 * k + 1] = v[ok]
+        g1[up, 2 * k + 1] = f1[k][ok]
+        g2[up, 2 * k + 1] = f2[k][ok]
+    return nbr, g1, g2
+
+
+KING_MOVES = ((1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1))
+
+
+def king_graph(side: int, lo: int = 1, hi: int = 16, seed: int = 7, M: int = 0) -> GraphInstance:
+    """side x side king's graph (the 8 neighbours of a square grid; slots in the order of
+    KING_MOVES), f1, f2 ~ U{lo..hi} per undirected edge (uint8), A = column x = 0,
+    B = column x = side - 1."""
+    V = side * side
+    v = np.arange(V, dtype=np.int64)
+    x, y = v % side, v // side
+    nbr = np.full((V, 8), -1, np.int64)
+    f1 = np.zeros((V, 8), np.uint8)
+    f2 = np.zeros((V, 8), np.uint8)
+    for j in range(0, 8, 2):            # each undirected edge drawn once, at its lower end
+        dx, dy = KING_MOVES[j]
+        if dy < 0 or (dy == 0 and dx < 0):
+            dx, dy = -dx, -dy
+        ok = (x + dx >= 0) & (x + dx < side) & (y + dy < side)
+        a = v[ok]
+        b = a + dx + dy * side
+        w1 = uniform_int(seed, 200 + j, V, lo, hi)[ok]
+        w2 = uniform_int(seed, 300 + j, V, lo, hi)[ok]
+        ja = KING_MOVES.index((dx, dy))
+        jb = KING_MOVES.index((-dx, -dy))
+        nbr[a, ja], nbr[b, jb] = b, a
+        f1[a, ja] = f1[b, jb] = w1
+        f2[a, ja] = f2[b, jb] = w2
+    A = v[x == 0]
+    B = v[x == side - 1]
+    return GraphInstance(nbr, f1, f2, A, B, M, f"king{side}_U{lo}_{hi}")
+
+
+def random_graph(V: int, rounds: int = 6, seed: int = 8, lo: int = 1, hi: int = 16, f2_lo: Optional[int] = None,
+                 drop: float = 0.0, dtype=np.uint8):
+    """A random graph of degree <= ``rounds`` (<= 8): round j pairs the vertices by a random
+    permutation (vertex p[2i] with p[2i+1]) and puts each new edge in slot j at both ends;
+    a pair already joined, and a fraction ``drop`` of the pairs, leave slot j empty.
+    f1 ~ U{lo..hi}, f2 ~ U{f2_lo..hi} per edge.  Returns (nbr, f1, f2)."""
+    f2_lo = lo if f2_lo is None else f2_lo
+    nbr = np.full((V, rounds), -1, np.int64)
+    f1 = np.zeros((V, rounds), dtype)
+    f2 = np.zeros((V, rounds), dtype)
+    seen = set()
+    for j in range(rounds):
+        p = np.argsort(u64(seed, 400 + j, V), kind="stable")
+        a, b = p[0:V - 1:2], p[1:V:2]
+        keep = uniform_unit(seed, 500 + j, a.size) >= drop
+        w1 = uniform_int(seed, 600 + j, a.size, lo, hi)
+        w2 = uniform_int(seed, 700 + j, a.size, f2_lo, hi)
+        for i in np.flatnonzero(keep).tolist():
+            e = (min(a[i], b[i]), max(a[i], b[i]))
+            if e in seen:
+                continue
+            seen.add(e)
+            nbr[a[i], j], nbr[b[i], j] = b[i], a[i]
+            f1[a[i], j] = f1[b[i], j] = w1[i]
+            f2[a[i], j] = f2[b[i], j] = w2[i]
+    return nbr, f1, f2
+
+
+def random_small_graph(seed: int, max_vertices: int = 12, rounds=(1, 4), f_hi: int = 6, M_max: int = 25,
+                       max_sources: Optional[int] = None, drop: float = 0.25) -> GraphInstance:
+    """A tiny random graph for brute-force comparisons: 2..max_vertices vertices, a number of
+    pairing rounds drawn from ``rounds`` with a fraction ``drop`` of the pairs left out,
+    f1 in [1, f_hi], f2 in [0 or 1, f_hi], random disjoint A (at most ``max_sources``,
+    default V/3) and B, M in [1, M_max]."""
+    r = u64(seed, S_SHAPE + 50, 8)
+    V = 2 + int(r[0] % np.uint64(max_vertices - 1))
+    nr = rounds[0] + int(r[1] % np.uint64(rounds[1] - rounds[0] + 1))
+    nbr, f1, f2 = random_graph(V, nr, seed, 1, f_hi, int(r[2] % np.uint64(2)), drop=drop)
+    perm = np.argsort(u64(seed, S_A + 50, V))
+    amax = max(1, V // 3) if max_sources is None else max_sources
+    nA = min(1 + int(r[3] % np.uint64(amax)), V - 1)
+    nB = min(1 + int(r[4] % np.uint64(max(1, (V - nA) // 2))), V - nA)
+    A = np.sort(perm[:nA]).astype(np.int64)
+    B = np.sort(perm[nA:nA + nB]).astype(np.int64)
+    M = int(1 + r[5] % np.uint64(M_max))
+    return GraphInstance(nbr, f1, f2, A, B, M, f"tinygraph{seed}")

@@ -47,9 +47,30 @@ def directed_edges(extents: Sequence[int], f1, f2):
     return adj, V
 
 
+def graph_directed_edges(nbr, f1, f2):
+    """{v: [(u, slot, f1, f2), ...]} from adjacency slots (nbr = -1: empty slot)."""
+    nbr = np.asarray(nbr)
+    V, S = nbr.shape
+    f1 = np.asarray(f1).reshape(V, S)
+    f2 = np.asarray(f2).reshape(V, S)
+    adj: Dict[int, list] = collections.defaultdict(list)
+    for v in range(V):
+        for j in range(S):
+            if nbr[v, j] >= 0:
+                adj[v].append((int(nbr[v, j]), j, int(f1[v, j]), int(f2[v, j])))
+    return adj, V
+
+
+def adjacency(inst):
+    """The directed edges of a lattice instance (extents) or a graph instance (nbr)."""
+    if hasattr(inst, "nbr"):
+        return graph_directed_edges(inst.nbr, inst.f1, inst.f2)
+    return directed_edges(inst.extents, inst.f1, inst.f2)
+
+
 def all_simple_paths(inst):
     """Yield (end, F1, F2, prev, dir) for every simple path starting in A (length >= 0)."""
-    adj, V = directed_edges(inst.extents, inst.f1, inst.f2)
+    adj, V = adjacency(inst)
     for a in sorted(set(int(x) for x in inst.A)):
         yield (a, 0, 0, -1, -1)
         on_path = {a}
@@ -89,7 +110,7 @@ def label_histories(inst):
     the (F1, F2) of all simple paths; the time F1 of the first improvement of a B vertex
     (None if none)."""
     M = int(inst.M)
-    adj, V = directed_edges(inst.extents, inst.f1, inst.f2)
+    adj, V = adjacency(inst)
     Aset = set(int(a) for a in inst.A)
     Bset = set(int(b) for b in inst.B)
     arrivals: Dict[int, List[Tuple[int, int]]] = collections.defaultdict(list)
@@ -143,7 +164,7 @@ def phantoms(inst) -> int:
 def pareto_trace(inst) -> np.ndarray:
     """(rows, 3) trace (Time, active vertices, flows) implied by the flow semantics."""
     M = int(inst.M)
-    adj, V = directed_edges(inst.extents, inst.f1, inst.f2)
+    adj, V = adjacency(inst)
     Aset = set(int(a) for a in inst.A)
     Bset = set(int(b) for b in inst.B)
     arrivals: Dict[int, List[Tuple[int, int]]] = collections.defaultdict(list)
@@ -266,3 +287,38 @@ def dijkstra_trace(extents, f1, A, B):
         rows.append((int(T), len(np.unique(src[live])), int(live.sum())))
     X = int(Bv[tb == F1].min()) if F1 is not None else -1
     return (int(F1) if F1 is not None else -1), X, t, np.array(rows, dtype=np.int64)
+
+
+def graph_tau(nbr, f1, A) -> np.ndarray:
+    """Multi-source first-passage times on a graph given by adjacency slots (scipy)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import dijkstra
+
+    nbr = np.asarray(nbr)
+    V, S = nbr.shape
+    ok = nbr >= 0
+    src = np.repeat(np.arange(V), S).reshape(V, S)[ok]
+    G = coo_matrix((np.asarray(f1).reshape(V, S)[ok].astype(np.float64), (src, nbr[ok])), shape=(V, V)).tocsr()
+    return dijkstra(G, directed=True, indices=np.asarray(A, dtype=np.int64), min_only=True)
+
+
+def graph_dijkstra_trace(nbr, f1, A, B):
+    """:func:`dijkstra_trace` on a graph given by adjacency slots (f2 = 0)."""
+    nbr = np.asarray(nbr)
+    V, S = nbr.shape
+    t = graph_tau(nbr, f1, A)
+    Bv = np.asarray(B, dtype=np.int64)
+    F1 = np.min(t[Bv])
+    ok = nbr >= 0
+    src = np.repeat(np.arange(V), S).reshape(V, S)[ok]
+    dst = nbr[ok]
+    finite = t[np.isfinite(t)]
+    times = np.unique(finite[finite > 0])
+    if np.isfinite(F1):
+        times = times[times <= F1]
+    rows = []
+    for T in [0.0] + list(times):
+        live = (t[src] <= T) & (t[dst] > T)
+        rows.append((int(T), len(np.unique(src[live])), int(live.sum())))
+    X = int(Bv[t[Bv] == F1].min()) if np.isfinite(F1) else -1
+    return (int(F1) if np.isfinite(F1) else -1), X, t, np.array(rows, dtype=np.int64)

@@ -326,6 +326,8 @@ def run_ours(args):
         line["open_problems"] = bench_open_problems(csp, synth)
     if world == 1 and args.fractal:
         line["fractal"] = bench_fractal(csp, synth)
+    if world == 1 and args.graphs:
+        line["graphs"] = bench_graphs(csp, synth)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, ORACLE_SAMPLE_CYCLES)
     print(json.dumps(line), flush=True)
@@ -447,6 +449,38 @@ def bench_fractal(csp, synth, t=4096):
     for x in rows:
         x["proof_N_t"] = n1 + (x["j"] - 1) * 4 * t / 15
     return {"workload": f"lattice2d_fractal_t{t}", "extents": [2 * t + 1, t + 2], "t": t, "rows": rows}
+
+
+def bench_graphs(csp, synth, side=2048):
+    """General graphs (csp_create_graph) against the lattice path: the 2-D side^2 lattice with
+    f1, f2 ~ U{1..16} (seed 31) solved natively and written as a graph (the same solve, so the
+    answers and counts must agree), and the king's graph of the same side (8 neighbours,
+    seed 32).  A = column 0, B = the last column, M = 6 side.  Wall time of the synchronous
+    call after one warm-up solve."""
+    ext = [side, side]
+    f1, f2 = synth.uniform_weights(ext, 1, 16, 31)
+    A, B, M = synth.face(ext, 0, 0), synth.face(ext, 0, side - 1), 6 * side
+    nbr, g1, g2 = synth.graph_from_lattice(ext, f1, f2)
+    king = synth.king_graph(side, 1, 16, seed=32)
+    out = {"workload": f"lattice2d_{side}_U16 native and as a graph; king{side}_U16", "M": M, "cases": []}
+    ref = None
+    for name, make, a, b in (("lattice (native)", lambda: csp.Lattice(ext, f1, f2), A, B),
+                             ("lattice as a graph", lambda: csp.Graph(nbr, g1, g2), A, B),
+                             ("king's graph", lambda: csp.Graph(king.nbr, king.f1, king.f2), king.A, king.B)):
+        h = make()
+        h.reserve()
+        h.solve(a, b, M)
+        t0 = time.perf_counter()
+        r = h.solve(a, b, M)
+        sec = time.perf_counter() - t0
+        h.close()
+        key = (r.answer(), r.cycles, r.updates, r.launched)
+        if ref is None:
+            ref = key
+        out["cases"].append({"case": name, "answer": list(r.answer()), "cycles": r.cycles, "updates": r.updates,
+                             "solve_s": sec, "updates_per_s": r.updates / sec,
+                             "same_as_native": key == ref if name == "lattice as a graph" else None})
+    return out
 
 
 def bench_batched(csp, synth):
@@ -574,6 +608,8 @@ def main():
     ap.add_argument("--batch", type=int, default=1, help="also measure 512 batched instances vs one launch each (N=1)")
     ap.add_argument("--open-problems", type=int, default=0,
                     help="also measure the mean active-set size vs time on 1024^2 i.i.d. lattices (N=1)")
+    ap.add_argument("--graphs", type=int, default=0,
+                    help="also time general graphs against the lattice path on 2048^2 (N=1)")
     ap.add_argument("--fractal", type=int, default=0,
                     help="also count the active vertices at time t = 4096 on the environments omega_j (N=1)")
     ap.add_argument("--anticorrelated", type=int, default=1,

@@ -19,6 +19,13 @@
  *   - direction dir = 2k + s leads from a vertex to its neighbour v + e_k (s = 0) or
  *     v - e_k (s = 1).
  *
+ * General graphs (csp_create_graph; Section 1 of the paper states the method for any
+ * graph, and the bounded degree is what the GPU layout needs): up to 8 edges per vertex,
+ * given as adjacency slots; the direction of an edge is its slot at the vertex it leaves.
+ * A graph handle works with csp_solve, csp_solve_async, csp_reserve, csp_get_labels,
+ * csp_reconstruct_path and csp_reconstruct_fast (the calls below that take a csp_lattice);
+ * csp_upload_weights, the batch API and the server API accept lattices only.
+ *
  * Every call returns a csp_status and never aborts.  Pointers named *_dev are device
  * pointers; all other pointers are host pointers.  Output buffers are owned by the
  * caller.  Calls on the same lattice must not overlap (a lattice owns one workspace).
@@ -50,7 +57,7 @@ typedef struct {
     int64_t F1;        /* minimal travel time F1(pi) subject to F2(pi) < M */
     int64_t X;         /* endpoint in B: largest label (smallest F2), then smallest id */
     int64_t x_src;     /* Y, the other end of the last edge x */
-    int64_t x_dir;     /* direction from Y to X (0 .. 2d-1) */
+    int64_t x_dir;     /* direction from Y to X (0 .. 2d-1; on a graph the slot of X at Y) */
     int64_t F2;        /* F2 of that path = M - Label(X) */
     int64_t cycles;    /* cycles run = distinct times at which some label improved */
     int64_t updates;   /* active-edge updates: sum over cycles of the flows alive at cycle start */
@@ -97,8 +104,21 @@ const char *csp_last_error(void);
 csp_status csp_create_lattice(int d, const int64_t *extents, const void *f1, const void *f2,
                               int weight_bytes, int on_device, void *stream, csp_lattice **out);
 
+/* Creates a general graph (the handle type is shared with lattices).  V in [1, 2^28);
+ * slots in [1, 8].  nbr[v * slots + j] is the neighbour of v in slot j, or -1 for an empty
+ * slot; f1[v * slots + j] >= 1 and f2[v * slots + j] are that edge's travel time and weight
+ * (uint8 or uint16 by weight_bytes; ignored in empty slots).  The graph is undirected:
+ * every edge sits in exactly one slot at each end, with the same f1 and f2, and there are
+ * no self loops or parallel edges.  All arrays are host arrays and stay the caller's; the
+ * library keeps per-vertex edge records and a neighbour table on the device (16 or 32 B +
+ * 32 B per vertex).  stream: cudaStream_t or NULL.
+ * Errors: CSP_ERR_INVALID (arguments, or a graph that breaks the rules above; the first
+ * offending vertex and slot are in csp_last_error), CSP_ERR_OOM, CSP_ERR_CUDA. */
+csp_status csp_create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void *f1, const void *f2,
+                            int weight_bytes, void *stream, csp_lattice **out);
+
 /* Overwrites the weights of an existing lattice (same layout and width as at creation),
- * without allocating.  on_device as above. */
+ * without allocating.  on_device as above.  CSP_ERR_INVALID on a graph. */
 csp_status csp_upload_weights(csp_lattice *lat, const void *f1, const void *f2, int on_device, void *stream);
 
 /* Frees the lattice and its workspace.  NULL is ignored. */
@@ -214,8 +234,8 @@ typedef struct csp_batch csp_batch;
 
 /* Allocates every instance's workspace, uploads the sets, plans the schedule and
  * captures the launch.  All lattices must use the same weight width.  The lattices must
- * outlive the batch.  Errors: CSP_ERR_INVALID (any query invalid on the host side),
- * CSP_ERR_OOM, CSP_ERR_CUDA. */
+ * outlive the batch.  Errors: CSP_ERR_INVALID (any query invalid on the host side, or a
+ * graph among the handles), CSP_ERR_OOM, CSP_ERR_CUDA. */
 csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_options *opt, csp_batch **out);
 
 /* Enqueues one run of the whole batch on stream (cudaStream_t or NULL); asynchronous. */
@@ -323,7 +343,8 @@ typedef struct {
 } csp_server_query;
 
 /* Allocates the slots and launches the persistent server kernel on its own stream.  The
- * lattice must outlive the server; while the server runs it occupies the GPU. */
+ * lattice must outlive the server; while the server runs it occupies the GPU.
+ * CSP_ERR_INVALID on a graph. */
 csp_status csp_server_create(csp_lattice *lat, const csp_server_options *opt, csp_server **out);
 
 /* The server's slots (groups), CTAs per slot and ring size. */

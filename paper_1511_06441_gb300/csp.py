@@ -64,6 +64,7 @@ def lib():
         L.csp_last_error.restype = ctypes.c_char_p
         L.csp_create_lattice.argtypes = [ctypes.c_int, i64p, vp, vp, ctypes.c_int, ctypes.c_int, vp,
                                          ctypes.POINTER(vp)]
+        L.csp_create_graph.argtypes = [i64, ctypes.c_int32, i64p, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
         L.csp_upload_weights.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.csp_destroy_lattice.argtypes = [vp]
         L.csp_destroy_lattice.restype = None
@@ -79,7 +80,8 @@ def lib():
         L.csp_reconstruct_fast.argtypes = [vp, i64p, i64, i64p, i64, i64, ctypes.POINTER(CspOptions), i64,
                                            ctypes.POINTER(CspResult), i64p, i64, i64p]
         L.csp_reconstruct_path.restype = ctypes.c_int
-        for f in ("csp_create_lattice", "csp_upload_weights", "csp_reserve", "csp_solve", "csp_solve_async",
+        for f in ("csp_create_lattice", "csp_create_graph", "csp_upload_weights", "csp_reserve", "csp_solve",
+                  "csp_solve_async",
                   "csp_get_labels", "csp_solve_static"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -262,6 +264,32 @@ class Lattice:
         out = np.zeros(self.V, np.int32)
         _check(lib().csp_get_labels(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "csp_get_labels")
         return out
+
+
+class Graph(Lattice):
+    """A general graph resident on the GPU (``csp_create_graph``): ``nbr`` (V, S) neighbour
+    ids (-1: empty slot), ``f1``/``f2`` (V, S) uint8 or uint16 the edge in each slot; S <= 8.
+    Undirected: every edge in one slot at each end with equal weights.  Solves and path
+    reconstruction work as on a lattice; x_dir is the slot of x at x_src."""
+
+    def __init__(self, nbr, f1, f2, stream=None):
+        nbr = np.ascontiguousarray(np.asarray(nbr, dtype=np.int64))
+        if nbr.ndim != 2:
+            raise ValueError("nbr must be (V, S)")
+        f1 = np.ascontiguousarray(f1)
+        f2 = np.ascontiguousarray(f2)
+        if f1.dtype != f2.dtype or f1.dtype not in (np.uint8, np.uint16) or f1.shape != nbr.shape or \
+                f2.shape != nbr.shape:
+            raise ValueError("f1 and f2 must match nbr's shape and both be uint8 or both uint16")
+        V, S = nbr.shape
+        self.extents = [V]
+        self.d = 0
+        self.weight_bytes = f1.dtype.itemsize
+        h = vp()
+        _check(lib().csp_create_graph(V, S, nbr.ctypes.data_as(i64p), f1.ctypes.data, f2.ctypes.data,
+                                      self.weight_bytes, _stream_handle(stream), ctypes.byref(h)), "csp_create_graph")
+        self._h = h
+        self.V = int(lib().csp_num_vertices(h))
 
 
 def result_from_record(rec) -> Result:

@@ -357,7 +357,7 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
     for (int64_t i = 0; i < n; i++) {
         const csp_query &x = q[i];
         if (!x.lat || !x.A || !x.B || x.nA < 1 || x.nB < 1 || x.M >= (1ll << 31) - 1 || x.M < -(1ll << 31) + 1 ||
-            x.lat->wbytes != wbytes)
+            x.lat->wbytes != wbytes || x.lat->d == GRAPH)  // lattices only
             return CSP_ERR_INVALID;
     }
     csp_batch *b = new (std::nothrow) csp_batch();

@@ -41,6 +41,10 @@ constexpr int NWARP = TPB / 32;
 constexpr int TIME_LIMIT = 1 << 30; // arrival times must stay below this
 constexpr int POOL_PAD = 64;        // extra elements after each pool array (bulk copies round up)
 constexpr int NSTAGE = 3;           // input stages of the sweep (tiles in flight per CTA)
+constexpr int GRAPH = 5;            // template value of D for a general graph (Section 1): up to 8 slots
+
+// Directions (edge slots) per vertex: 2d on a lattice of dimension d, 8 on a general graph.
+__host__ __device__ constexpr int nslots(int D) { return D == GRAPH ? 8 : 2 * D; }
 
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_OOM = 2, ST_CUDA = 3, ST_CAPACITY = 4, ST_TIMEOUT = 5, ST_BARRIER = 6 };
 
@@ -85,13 +89,14 @@ struct Control {
     alignas(128) long long out[R_COUNT];
 };
 
-// Per-vertex edge record: (f1, f2) of the 2d edges of a vertex in direction order,
-// f1 = 0 for a missing edge (absent, or leaving the box).  8-bit weights: 2 bytes per
-// direction, one 16-byte record for d <= 4.  16-bit weights: 4 bytes per direction,
-// 16 bytes for d <= 2 and 32 bytes for d <= 4.
+// Per-vertex edge record: (f1, f2) of the edges of a vertex in direction (slot) order,
+// f1 = 0 for a missing edge (absent, leaving the box, or an empty slot of a graph).
+// 8-bit weights: 2 bytes per direction, one 16-byte record for up to 8 directions (d <= 4,
+// or a graph).  16-bit weights: 4 bytes per direction, 16 bytes for d <= 2 and 32 bytes
+// for up to 8 directions.
 template <typename W, int D>
 struct EdgeRecord {
-    static constexpr int BYTES = (int)sizeof(W) * 2 * 2 * D <= 16 ? 16 : 32;
+    static constexpr int BYTES = (int)sizeof(W) * 2 * nslots(D) <= 16 ? 16 : 32;
     static constexpr int VEC = BYTES / 16;  // uint4 loads per record
     uint4 raw[VEC];
     __device__ __forceinline__ int f1(int dir) const
@@ -111,7 +116,8 @@ struct Params {
     const W *f1, *f2;              // [d][V] travel time, weight of edge (v, v + e_k)
     const uint4 *rec;              // per-vertex edge records (EdgeRecord<W, d>)
     long long V;
-    int stride[4];
+    int stride[4];                 // lattice strides (unused on a graph)
+    const uint32_t *nbw;           // graph only: [8 V] slot j of v = neighbour << 3 | the slot of v there
     int32_t *label;
     unsigned long long *offer;
     const uint32_t *isB;
@@ -188,14 +194,46 @@ __device__ __forceinline__ int dir_offset(const int (&stride)[4], unsigned r)
 }
 
 
-// x code of a flow arriving at dst from direction r (r = direction from dst back to the
-// source): ~(src * 8 + dir), dir = r ^ 1 the direction from the source to dst.
-template <int D>
-__device__ __forceinline__ uint32_t arrival_code(const int (&stride)[4], uint32_t ed)
+// Neighbour of v in direction dir.  On a lattice v +- stride (outside the box where the
+// edge leaves it: callers check the record's f1 first or clamp); on a graph the slot's
+// neighbour (an empty slot holds v itself).
+template <int D, typename W>
+__device__ __forceinline__ uint32_t neighbour(const Params<W> &P, uint32_t v, unsigned dir)
 {
-    const uint32_t dst = ed >> 3, r = ed & 7u;
-    const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(stride, r));
-    return 0xffffffffu - (src * 8u + (r ^ 1u));
+    if constexpr (D == GRAPH) return __ldg(P.nbw + (size_t)v * 8 + dir) >> 3;
+    else return v + dir_offset<D>(P.stride, dir);
+}
+
+// Flow word of water leaving v in direction dir: dst << 3 | the direction from dst back to v.
+template <int D, typename W>
+__device__ __forceinline__ uint32_t flow_word(const Params<W> &P, uint32_t v, unsigned dir)
+{
+    if constexpr (D == GRAPH) return __ldg(P.nbw + (size_t)v * 8 + dir);
+    else return ((v + dir_offset<D>(P.stride, dir)) << 3) | (dir ^ 1u);
+}
+
+// Source of flow word ed and the flow's direction at its source.
+template <int D, typename W>
+__device__ __forceinline__ uint32_t flow_source(const Params<W> &P, uint32_t ed, uint32_t &sdir)
+{
+    if constexpr (D == GRAPH) {
+        const uint32_t x = __ldg(P.nbw + (size_t)(ed >> 3) * 8 + (ed & 7u));
+        sdir = x & 7u;
+        return x >> 3;
+    } else {
+        sdir = (ed & 7u) ^ 1u;
+        return (uint32_t)((int)(ed >> 3) + dir_offset<D>(P.stride, ed & 7u));
+    }
+}
+
+// x code of the flow with word ed arriving at its destination: ~(src * 8 + dir), dir the
+// direction from the source to the destination.
+template <int D, typename W>
+__device__ __forceinline__ uint32_t arrival_code(const Params<W> &P, uint32_t ed)
+{
+    uint32_t sdir;
+    const uint32_t src = flow_source<D>(P, ed, sdir);
+    return 0xffffffffu - (src * 8u + sdir);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns()
@@ -613,8 +651,8 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
             bool keep = false, arr = false;
             const bool live = q > L[i];  // (padding has q = 0 <= INT_MAX)
             if (TRACE && live) {  // the source is active in this pass (a plain store: every writer agrees)
-                const uint32_t src = (uint32_t)((int)(e[i] >> 3) + dir_offset<D>(P.stride, e[i] & 7u));
-                P.src_stamp[src] = stamp;
+                uint32_t sdir;
+                P.src_stamp[flow_source<D>(P, e[i], sdir)] = stamp;
             }
             if (live) {
                 st.live++;
@@ -622,16 +660,16 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
                 const int32_t t = sm.in_ta[s][j];
                 if (t == Tg) {
                     const unsigned long long key =
-                        ((unsigned long long)(uint32_t)q << 32) | arrival_code<D>(P.stride, e[i]);
+                        ((unsigned long long)(uint32_t)q << 32) | arrival_code<D>(P, e[i]);
                     atomicMax(P.offer + dst, key);
                     arr = true;
                 } else {
                     keep = true;
                     st.min_ta = min(st.min_ta, t);
                     if (TRACE && P.edge_stamp) {  // this directed edge still carries a flow when the cycle launches
-                        const uint32_t r = e[i] & 7u;
-                        const uint32_t src = (uint32_t)((int)dst + dir_offset<D>(P.stride, r));
-                        P.edge_stamp[(size_t)src * (2 * D) + (r ^ 1u)] = stamp;
+                        uint32_t sdir;
+                        const uint32_t src = flow_source<D>(P, e[i], sdir);
+                        P.edge_stamp[(size_t)src * nslots(D) + sdir] = stamp;
                     }
                 }
             }
@@ -712,25 +750,24 @@ __device__ __forceinline__ EdgeRecord<W, D> load_record(const uint4 *rec, uint32
 
 // Label of every neighbour of v (clamped index where the edge leaves the box; the value
 // is then ignored because the record's f1 is 0).
-template <int D>
-__device__ __forceinline__ void neighbour_labels(const unsigned long long *offer, const int (&stride)[4], uint32_t V,
-                                                 uint32_t v, int (&Lw)[2 * D])
+template <int D, typename W>
+__device__ __forceinline__ void neighbour_labels(const Params<W> &P, uint32_t V, uint32_t v, int (&Lw)[nslots(D)])
 {
 #pragma unroll
-    for (int dir = 0; dir < 2 * D; dir++) {
-        const uint32_t w = v + dir_offset<D>(stride, dir);
-        Lw[dir] = __ldcg(reinterpret_cast<const int *>(offer + (w < V ? w : v)) + 1);  // label half of offer[w]
+    for (int dir = 0; dir < nslots(D); dir++) {
+        const uint32_t w = neighbour<D>(P, v, dir);
+        Lw[dir] = __ldcg(reinterpret_cast<const int *>(P.offer + (w < V ? w : v)) + 1);  // label half of offer[w]
     }
 }
 
 // Water of quality Lv leaves v along each edge (v, w) with Lv - f2 > Label(w): returns
 // the bit mask of those directions (Steps 4-5).
 template <typename W, int D>
-__device__ __forceinline__ uint32_t launch_mask(const EdgeRecord<W, D> &r, int Lv, const int (&Lw)[2 * D])
+__device__ __forceinline__ uint32_t launch_mask(const EdgeRecord<W, D> &r, int Lv, const int (&Lw)[nslots(D)])
 {
     uint32_t mask = 0;
 #pragma unroll
-    for (int dir = 0; dir < 2 * D; dir++)
+    for (int dir = 0; dir < nslots(D); dir++)
         if (r.f1(dir) != 0 && Lv - r.f2(dir) > Lw[dir]) mask |= 1u << dir;
     return mask;
 }
@@ -757,11 +794,10 @@ __device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters 
     st.written += lane == 0 ? total : 0u;
     uint32_t p = sp.f0 + incl - nk;
 #pragma unroll
-    for (int dir = 0; dir < 2 * D; dir++)
+    for (int dir = 0; dir < nslots(D); dir++)
         if (mask & (1u << dir)) {
-            const uint32_t w = v + dir_offset<D>(P.stride, dir);
             const int t = Time + r.f1(dir);
-            put_flow(P, ob, C, sp, p, (w << 3) | (uint32_t)(dir ^ 1), Lv - r.f2(dir), t);
+            put_flow(P, ob, C, sp, p, flow_word<D>(P, v, dir), Lv - r.f2(dir), t);
             p++;
             st.min_ta = min(st.min_ta, t);
             st.launched++;
@@ -801,11 +837,11 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
         if (j < n_cand) {
             const uint32_t ec = __ldcg(P.cand + cand_base + j);
             v = ec >> 3;
-            code = arrival_code<D>(P.stride, ec);
+            code = arrival_code<D>(P, ec);
             const unsigned long long ov = __ldcg(P.offer + v);
             r = load_record<W, D>(P.rec, v);
-            int Lw[2 * D];
-            neighbour_labels<D>(P.offer, P.stride, V, v, Lw);
+            int Lw[nslots(D)];
+            neighbour_labels<D>(P, V, v, Lw);
             const uint32_t bw = __ldcg(P.isB + (v >> 5));  // (issued with the other loads)
             if (lo32(ov) == code) {  // the winning arrival at v
                 won = true;
@@ -824,9 +860,9 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
                 mask = launch_mask<W, D>(r, Lv, Lw);
                 if (TRACE && P.edge_stamp) {  // a flow started on an edge that still carries one is a phantom (Step 5)
 #pragma unroll
-                    for (int dir = 0; dir < 2 * D; dir++)
+                    for (int dir = 0; dir < nslots(D); dir++)
                         if ((mask >> dir) & 1u)
-                            st.phantoms += __ldcg(P.edge_stamp + (size_t)v * (2 * D) + dir) == stamp;
+                            st.phantoms += __ldcg(P.edge_stamp + (size_t)v * nslots(D) + dir) == stamp;
                 }
             }
         }
@@ -860,8 +896,8 @@ __device__ CSP_PHASE_INLINE void seed(const Params<W> &P, const Group &g, uint32
         if (j < n_src) {
             v = __ldcg(P.cand + j);
             r = load_record<W, D>(P.rec, v);
-            int Lw[2 * D];
-            neighbour_labels<D>(P.offer, P.stride, V, v, Lw);
+            int Lw[nslots(D)];
+            neighbour_labels<D>(P, V, v, Lw);
             mask = launch_mask<W, D>(r, P.M, Lw);
         }
         emit_flows<W, D>(P, 0, C, sm, v, P.M, r, mask, 0, st);

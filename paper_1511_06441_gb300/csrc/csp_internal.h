@@ -21,18 +21,19 @@ extern thread_local std::string g_last_error;
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
-inline int record_bytes(int d, int wbytes) { return wbytes * 4 * d <= 16 ? 16 : 32; }
+inline int record_bytes(int d, int wbytes) { return wbytes * 2 * csp::nslots(d) <= 16 ? 16 : 32; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct csp_lattice {
-    int d = 0;
+    int d = 0;                          // lattice dimension 1..4, or csp::GRAPH
     int wbytes = 1;
     int64_t ext[4] = {1, 1, 1, 1};
     int stride[4] = {0, 0, 0, 0};
     int64_t V = 0;
     int device = 0;
-    void *f1 = nullptr, *f2 = nullptr;  // device [d][V]
+    void *f1 = nullptr, *f2 = nullptr;  // device [d][V] (lattice only)
     void *rec = nullptr;                // device per-vertex edge records
+    uint32_t *nbw = nullptr;            // graph only: device [8 V] neighbour << 3 | back slot
     int rec_bytes = 16;
     unsigned long long flow_bound = 0;  // sum of f1 over directed edges: max flows alive
     // workspace of csp_solve / csp_solve_async

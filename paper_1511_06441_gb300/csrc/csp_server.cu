@@ -266,7 +266,7 @@ extern "C" {
 
 csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_server **out)
 {
-    if (!L || !out) return CSP_ERR_INVALID;
+    if (!L || !out || L->d == GRAPH) return CSP_ERR_INVALID;  // lattices only
     *out = nullptr;
     csp_server *s = new (std::nothrow) csp_server();
     if (!s) return CSP_ERR_OOM;

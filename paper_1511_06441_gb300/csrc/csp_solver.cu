@@ -173,7 +173,7 @@ __global__ void k_mark_A(const int64_t *A, long long nA, const uint32_t *isB, lo
 // out[0] = path length (X first), out[1] = status (0, or CSP_ERR_CAPACITY if a needed log
 // record was dropped, or CSP_ERR_CUDA if the record is inconsistent).
 template <typename W>
-__global__ void k_backtrack(const W *f1, long long V, int d, int s0, int s1, int s2, int s3, long long X, long long F1,
+__global__ void k_backtrack(const unsigned char *rec, int rec_bytes, int nslot, long long V, long long X, long long F1,
                             uint32_t code0, const int32_t *first_t, const uint32_t *first_code, const uint2 *log,
                             unsigned long long log_cap, const int32_t *pass_time, const unsigned long long *pass_off,
                             long long n_pass, long long *path, long long cap, long long *out)
@@ -182,7 +182,6 @@ __global__ void k_backtrack(const W *f1, long long V, int d, int s0, int s1, int
     __shared__ unsigned long long s_lo, s_hi;
     __shared__ uint32_t s_code;
     __shared__ int s_mode, s_status, s_found;
-    const int stride[4] = {s0, s1, s2, s3};
     if (threadIdx.x == 0) {
         s_v = X;
         s_t = F1;
@@ -197,9 +196,10 @@ __global__ void k_backtrack(const W *f1, long long V, int d, int s0, int s1, int
             s_mode = 0;  // 0: next step, 1: scan the log, 2: stop
             const uint32_t sd = 0xffffffffu - s_code;
             const long long src = sd >> 3;
-            const int dir = (int)(sd & 7u), k = dir >> 1;
-            const long long lo = (dir & 1) ? src - stride[k] : src;  // lower end of the edge
-            const long long f = (src < V && k < d && lo >= 0 && lo < V) ? (long long)f1[(long long)k * V + lo] : 0;
+            const int dir = (int)(sd & 7u);
+            // f1 of x from the edge record of its source (0: no such edge)
+            const long long f =
+                (src < V && dir < nslot) ? (long long)reinterpret_cast<const W *>(rec + src * rec_bytes)[2 * dir] : 0;
             const long long ty = s_t - f;
             if (s_n < cap) path[s_n] = src;
             s_n++;
@@ -294,6 +294,7 @@ const void *pick_kernel_w(int d)
     case 1: return kernel_ptr<1, W, TRACE>();
     case 2: return kernel_ptr<2, W, TRACE>();
     case 3: return kernel_ptr<3, W, TRACE>();
+    case GRAPH: return kernel_ptr<GRAPH, W, TRACE>();
     default: return kernel_ptr<4, W, TRACE>();
     }
 }
@@ -326,7 +327,7 @@ csp_status ensure_workspace(csp_lattice *L, int64_t pool_cap, int64_t sets_cap)
     // can run out of room (a CTA lists at most the flows of its ceil(chunks / CTAs) chunks)
     const int64_t cand_cap = std::max<int64_t>(V, pool_cap + (int64_t)max_group_ctas(L->device) * TILE);
     const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
-                 o_stamp = take(((V + 3) / 4) * 16), o_estamp = take(2 * L->d * V * 4), o_cand = take(cand_cap * 4), o_ctl = take(sizeof(Control)),
+                 o_stamp = take(((V + 3) / 4) * 16), o_estamp = take((size_t)nslots(L->d) * V * 4), o_cand = take(cand_cap * 4), o_ctl = take(sizeof(Control)),
                  o_trace = take(trace_cap * 24), o_sets = take(sets_cap * 8);
     size_t o_pool[2][3], o_fill[2];
     for (int b = 0; b < 2; b++) {
@@ -386,7 +387,7 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
     CSP_CUDA(cudaMemsetAsync(L->isB, 0, ((V + 31) / 32) * 4, s));
     const bool phantoms = trace_dev && opt && (opt->flags & CSP_OPT_PHANTOMS);
     if (trace_dev) CSP_CUDA(cudaMemsetAsync(L->src_stamp, 0, ((V + 3) / 4) * 16, s));  // stamps are pass numbers >= 1
-    if (phantoms) CSP_CUDA(cudaMemsetAsync(L->edge_stamp, 0, 2 * L->d * V * 4, s));
+    if (phantoms) CSP_CUDA(cudaMemsetAsync(L->edge_stamp, 0, (size_t)nslots(L->d) * V * 4, s));
     const int sms = num_sms(L->device);
     k_reset<<<1, 32, 0, s>>>(L->ctl);
     k_mark_B<<<std::max<int64_t>(1, std::min<int64_t>(sms * 4, (nB + 255) / 256)), 256, 0, s>>>(B_dev, nB, L->isB, V,
@@ -400,7 +401,7 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
 
     const bool trace = trace_dev != nullptr;
     const void *fn = pick_kernel(L->d, L->wbytes, trace);
-    static thread_local bool attr_set[2][2][5] = {};
+    static thread_local bool attr_set[2][2][GRAPH + 1] = {};
     bool &done = attr_set[L->wbytes - 1][trace][L->d];
     if (!done) {
         CSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
@@ -425,6 +426,7 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         P.rec = (const uint4 *)L->rec;
         P.V = V;
         for (int k = 0; k < 4; k++) P.stride[k] = L->stride[k];
+        P.nbw = L->nbw;
         P.label = L->label;
         P.offer = L->offer;
         P.isB = L->isB;
@@ -557,9 +559,86 @@ csp_status csp_create_lattice(int d, const int64_t *extents, const void *f1, con
     return CSP_OK;
 }
 
+csp_status csp_create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void *f1, const void *f2,
+                            int weight_bytes, void *stream, csp_lattice **out)
+{
+    if (!out || !nbr || !f1 || !f2 || V < 1 || V >= (1ll << 28) || slots < 1 || slots > 8 ||
+        (weight_bytes != 1 && weight_bytes != 2))
+        return CSP_ERR_INVALID;
+    *out = nullptr;
+    auto w1 = [&](int64_t i) -> int64_t {
+        return weight_bytes == 1 ? ((const uint8_t *)f1)[i] : ((const uint16_t *)f1)[i];
+    };
+    auto w2 = [&](int64_t i) -> int64_t {
+        return weight_bytes == 1 ? ((const uint8_t *)f2)[i] : ((const uint16_t *)f2)[i];
+    };
+    // Every edge must sit in one slot at each end with the same weights; the slot at the
+    // other end becomes the back direction of the flow word.
+    const int rb = record_bytes(GRAPH, weight_bytes);
+    std::vector<uint32_t> nbw((size_t)V * 8);
+    std::vector<unsigned char> rec((size_t)V * rb, 0);
+    unsigned long long bound = 0;
+    for (int64_t v = 0; v < V; v++) {
+        for (int j = 0; j < 8; j++) nbw[(size_t)v * 8 + j] = (uint32_t)v << 3;  // empty: v itself, f1 = 0
+        for (int j = 0; j < slots; j++) {
+            const int64_t i = v * slots + j, u = nbr[i];
+            if (u == -1) continue;
+            const char *why = nullptr;
+            int back = -1;
+            if (u < 0 || u >= V) why = "neighbour id out of range";
+            else if (u == v) why = "self loop";
+            else if (w1(i) < 1) why = "travel time below 1";
+            for (int k = 0; k < j && !why; k++)
+                if (nbr[v * slots + k] == u) why = "parallel edge";
+            for (int k = 0; k < slots && !why; k++)
+                if (nbr[u * slots + k] == v) {
+                    if (w1(u * slots + k) != w1(i) || w2(u * slots + k) != w2(i)) why = "weights differ at the two ends";
+                    back = k;
+                }
+            if (!why && back < 0) why = "edge missing at its other end";
+            if (why) {
+                set_error("csp_create_graph: vertex " + std::to_string(v) + " slot " + std::to_string(j) + ": " + why);
+                return CSP_ERR_INVALID;
+            }
+            nbw[(size_t)v * 8 + j] = ((uint32_t)u << 3) | (uint32_t)back;
+            unsigned char *r = rec.data() + (size_t)v * rb;
+            if (weight_bytes == 1) {
+                r[2 * j] = (uint8_t)w1(i);
+                r[2 * j + 1] = (uint8_t)w2(i);
+            } else {
+                ((uint16_t *)r)[2 * j] = (uint16_t)w1(i);
+                ((uint16_t *)r)[2 * j + 1] = (uint16_t)w2(i);
+            }
+            bound += (unsigned long long)w1(i);
+        }
+    }
+    csp_lattice *L = new (std::nothrow) csp_lattice();
+    if (!L) return CSP_ERR_OOM;
+    L->d = GRAPH;
+    L->wbytes = weight_bytes;
+    L->V = V;
+    L->ext[0] = V;
+    L->rec_bytes = rb;
+    L->flow_bound = bound;
+    cudaGetDevice(&L->device);
+    cudaError_t e = cudaMalloc(&L->rec, rec.size());
+    if (e == cudaSuccess) e = cudaMalloc((void **)&L->nbw, nbw.size() * 4);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L->rec, rec.data(), rec.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L->nbw, nbw.data(), nbw.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        csp_destroy_lattice(L);
+        return cuda_fail(e, "csp_create_graph");
+    }
+    *out = L;
+    return CSP_OK;
+}
+
 csp_status csp_upload_weights(csp_lattice *L, const void *f1, const void *f2, int on_device, void *stream)
 {
-    if (!L || !f1 || !f2) return CSP_ERR_INVALID;
+    if (!L || !f1 || !f2 || L->d == GRAPH) return CSP_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)L->d * L->V * L->wbytes;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -599,6 +678,7 @@ void csp_destroy_lattice(csp_lattice *L)
     if (L->f1) cudaFree(L->f1);
     if (L->f2) cudaFree(L->f2);
     if (L->rec) cudaFree(L->rec);
+    if (L->nbw) cudaFree(L->nbw);
     if (L->ws) cudaFree(L->ws);
     delete L;
 }
@@ -800,13 +880,13 @@ csp_status csp_reconstruct_fast(csp_lattice *L, const int64_t *A, int64_t nA, co
         const uint32_t code0 = 0xffffffffu - (uint32_t)(res->x_src * 8 + res->x_dir);
         long long *dpath = (long long *)(b + o_path), *dout = (long long *)(b + o_out);
         if (L->wbytes == 1)
-            k_backtrack<uint8_t><<<1, 512, 0, s>>>((const uint8_t *)L->f1, V, L->d, L->stride[0], L->stride[1],
-                                                   L->stride[2], L->stride[3], res->X, res->F1, code0, rl.first_t,
+            k_backtrack<uint8_t><<<1, 512, 0, s>>>((const unsigned char *)L->rec, L->rec_bytes, nslots(L->d), V,
+                                                   res->X, res->F1, code0, rl.first_t,
                                                    rl.first_code, rl.log, rl.log_cap, rl.pass_time, rl.pass_off, n_pass,
                                                    dpath, cap, dout);
         else
-            k_backtrack<uint16_t><<<1, 512, 0, s>>>((const uint16_t *)L->f1, V, L->d, L->stride[0], L->stride[1],
-                                                    L->stride[2], L->stride[3], res->X, res->F1, code0, rl.first_t,
+            k_backtrack<uint16_t><<<1, 512, 0, s>>>((const unsigned char *)L->rec, L->rec_bytes, nslots(L->d), V,
+                                                    res->X, res->F1, code0, rl.first_t,
                                                     rl.first_code, rl.log, rl.log_cap, rl.pass_time, rl.pass_off,
                                                     n_pass, dpath, cap, dout);
         long long o[2] = {0, 0};

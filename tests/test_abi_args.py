@@ -77,3 +77,43 @@ def test_static_entry_point_rejects_bad_shapes(lib):
     assert lib.csp_solve_static(2, _p(big), vp(1), vp(1), 1, vp(1), i64(1), vp(1), i64(1), i64(10), i64(0), None,
                                 vp(1)) == INVALID
     del A
+
+
+def _graph(lib, nbr, f1, f2=None, slots=None, wb=1):
+    nbr = np.ascontiguousarray(np.asarray(nbr, np.int64))
+    f1 = np.ascontiguousarray(np.asarray(f1, np.uint8 if wb == 1 else np.uint16))
+    f2 = np.zeros_like(f1) if f2 is None else np.ascontiguousarray(np.asarray(f2, f1.dtype))
+    out = vp()
+    st = lib.csp_create_graph(i64(nbr.shape[0]), ctypes.c_int32(nbr.shape[1] if slots is None else slots), _p(nbr),
+                              f1.ctypes.data_as(vp), f2.ctypes.data_as(vp), wb, None, ctypes.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("nbr,f1,f2", [
+    ([[1, -1], [2, -1], [-1, -1]], [[1, 0], [1, 0], [0, 0]], None),        # 1-2 listed only at 1
+    ([[5, -1], [0, -1]], [[1, 0], [1, 0]], None),                          # id out of range
+    ([[0, -1], [-1, -1]], [[1, 0], [0, 0]], None),                         # self loop
+    ([[1, 1], [0, 0]], [[1, 1], [1, 1]], None),                            # parallel edges
+    ([[1, -1], [0, -1]], [[1, 0], [2, 0]], None),                          # f1 differs at the two ends
+    ([[1, -1], [0, -1]], [[1, 0], [1, 0]], [[3, 0], [4, 0]]),              # f2 differs at the two ends
+    ([[1, -1], [0, -1]], [[0, 0], [0, 0]], None),                          # travel time 0 on an edge
+    ([[-2, -1], [-1, -1]], [[1, 0], [0, 0]], None),                        # neither an id nor -1
+])
+def test_create_graph_rejects_broken_graphs(lib, nbr, f1, f2):
+    st, out = _graph(lib, nbr, f1, f2)
+    assert st == INVALID and not out.value
+    lib.csp_last_error.restype = ctypes.c_char_p
+    assert b"csp_create_graph: vertex" in lib.csp_last_error()
+
+
+def test_create_graph_rejects_bad_shapes(lib):
+    ok_nbr, ok_f1 = [[1], [0]], [[1], [1]]
+    assert _graph(lib, ok_nbr, ok_f1, slots=0)[0] == INVALID
+    assert _graph(lib, ok_nbr, ok_f1, slots=9)[0] == INVALID
+    assert _graph(lib, ok_nbr, ok_f1, wb=3)[0] == INVALID
+    nbr = np.zeros((0, 1), np.int64)
+    assert _graph(lib, nbr, np.zeros((0, 1)))[0] == INVALID
+    out = vp()
+    f = np.ones(2, np.uint8)
+    assert lib.csp_create_graph(i64(2), ctypes.c_int32(1), None, f.ctypes.data_as(vp), f.ctypes.data_as(vp), 1, None,
+                                ctypes.byref(out)) == INVALID

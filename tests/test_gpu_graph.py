@@ -1,0 +1,153 @@
+"""GPU parity on general graphs (csp_create_graph): the CUDA path against the oracle's
+graph form, element by element (answer, cycles, updates, flows started, trace, phantoms,
+labels), on tiny random graphs (one CTA and several), phantom-rich tiny graphs, king's
+graphs with 8- and 16-bit weights, a medium random graph spanning many pool tiles, a
+lattice written as a graph (equal to the lattice path too), first passage at size, and
+path reconstruction.  All results are integers: the tolerance is zero.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import brute
+import oracle
+from paper_1511_06441_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def csp():
+    from paper_1511_06441_gb300 import build, csp as mod
+    build.build()
+    return mod
+
+
+def _pair(csp, nbr, f1, f2, A, B, M, ctas=0, labels=True):
+    want = oracle.cycle_graph(nbr, f1, f2, A, B, M, labels=labels)
+    g = csp.Graph(nbr, f1, f2)
+    got = g.solve(A, B, M, trace=True, ctas=ctas, phantoms=True, trace_cap=1 << 17)
+    assert got.answer() == want.answer()
+    assert (got.cycles, got.updates, got.launched) == (want.cycles, want.updates, want.launched)
+    np.testing.assert_array_equal(got.trace, want.trace)
+    assert got.phantoms == want.phantoms
+    if labels:
+        np.testing.assert_array_equal(g.labels(), want.labels.astype(np.int32))
+    g.close()
+    return got
+
+
+@pytest.mark.parametrize("seed", range(120))
+def test_tiny_graph_one_cta(csp, seed):
+    t = synth.random_small_graph(seed)
+    _pair(csp, t.nbr, t.f1, t.f2, t.A, t.B, t.M, ctas=1)
+
+
+@pytest.mark.parametrize("seed", range(0, 120, 4))
+def test_tiny_graph_many_ctas(csp, seed):
+    t = synth.random_small_graph(seed)
+    _pair(csp, t.nbr, t.f1, t.f2, t.A, t.B, t.M, ctas=7)
+
+
+def test_phantom_rich_tiny_graphs(csp):
+    seen = 0
+    for seed in range(200):
+        t = synth.random_small_graph(seed, max_vertices=20, rounds=(3, 4), f_hi=20, M_max=150, max_sources=2,
+                                     drop=0.2)
+        seen += _pair(csp, t.nbr, t.f1, t.f2, t.A, t.B, t.M).phantoms > 0
+    assert seen >= 5
+
+
+@pytest.mark.parametrize("side,M,wide", [(64, 300, False), (256, 900, False), (128, 200000, True)])
+def test_king_graph(csp, side, M, wide):
+    g = synth.king_graph(side, 1, 16, seed=side)
+    f1, f2 = g.f1, g.f2
+    if wide:  # 16-bit weights: f2 spread over [1, 4000]
+        f1 = f1.astype(np.uint16)
+        f2 = (f2.astype(np.uint16) * 250)
+        f2[g.nbr < 0] = 0
+    got = _pair(csp, g.nbr, f1, f2, g.A, g.B, M)
+    assert got.F1 > 0
+
+
+def test_medium_random_graph_spans_many_tiles(csp):
+    nbr, f1, f2 = synth.random_graph(150_000, 6, seed=21, lo=1, hi=16, drop=0.1)
+    A = np.arange(0, 150_000, 30_011)
+    tau = brute.graph_tau(nbr, f1, A)
+    B = np.argsort(-np.where(np.isfinite(tau), tau, -1), kind="stable")[:4]  # the last vertices water reaches
+    got = _pair(csp, nbr, f1, f2, A, B, 120)
+    assert got.F1 > 0 and int(got.trace[:, 2].max()) > 20 * 2048 and got.phantoms > 0
+
+
+@pytest.mark.parametrize("which", ["64x64", "cube20"])
+def test_lattice_as_graph_equals_lattice_path(csp, which):
+    if which == "64x64":
+        inst = synth.workload_64x64()
+        Ms = (200, 400, 1000)
+    else:
+        ext = [20, 20, 20]
+        f1, f2 = synth.uniform_weights(ext, 1, 16, 9)
+        inst = synth.Instance(ext, f1, f2, synth.face(ext, 0, 0), synth.face(ext, 0, 19), 0)
+        Ms = (150, 400)
+    nbr, g1, g2 = synth.graph_from_lattice(inst.extents, inst.f1, inst.f2)
+    lat = csp.Lattice(inst.extents, inst.f1, inst.f2)
+    gr = csp.Graph(nbr, g1, g2)
+    for M in Ms:
+        a = lat.solve(inst.A, inst.B, M, trace=True, phantoms=True)
+        b = gr.solve(inst.A, inst.B, M, trace=True, phantoms=True)
+        assert a.answer() == b.answer() and (a.cycles, a.updates, a.launched, a.phantoms) == \
+            (b.cycles, b.updates, b.launched, b.phantoms)
+        np.testing.assert_array_equal(a.trace, b.trace)
+        np.testing.assert_array_equal(lat.labels(), gr.labels())
+    lat.close()
+    gr.close()
+
+
+def test_first_passage_on_a_king_graph(csp):
+    g = synth.king_graph(256, 1, 9, seed=5)
+    f2 = np.zeros_like(g.f2)
+    F1, X, tau, rows = brute.graph_dijkstra_trace(g.nbr, g.f1, g.A, g.B)
+    gr = csp.Graph(g.nbr, g.f1, f2)
+    got = gr.solve(g.A, g.B, 2**31 - 2, trace=True, trace_cap=1 << 15)
+    assert (got.F1, got.X, got.F2) == (F1, X, 0)
+    np.testing.assert_array_equal(got.trace, rows)
+    gr.close()
+
+
+@pytest.mark.parametrize("seed", range(0, 40))
+def test_graph_reconstruction_equals_oracle(csp, seed):
+    t = synth.random_small_graph(seed, max_vertices=16, rounds=(2, 4))
+    want_r = oracle.cycle_graph(t.nbr, t.f1, t.f2, t.A, t.B, t.M, trace=False)
+    want, _ = oracle.reconstruct_graph(t.nbr, t.f1, t.f2, t.A, t.B, t.M, first=want_r)
+    g = csp.Graph(t.nbr, t.f1, t.f2)
+    got = g.reconstruct(t.A, t.B, t.M)
+    fast, r = g.reconstruct_fast(t.A, t.B, t.M)
+    g.close()
+    if want is None:
+        assert got is None and fast is None and r.F1 == -1
+    else:
+        assert list(got) == want and list(fast) == want
+
+
+def test_king_graph_fast_path_equals_repeated_application(csp):
+    g = synth.king_graph(48, 1, 16, seed=3)
+    gr = csp.Graph(g.nbr, g.f1, g.f2)
+    slow = gr.reconstruct(g.A, g.B, 400)
+    fast, r = gr.reconstruct_fast(g.A, g.B, 400)
+    gr.close()
+    assert r.F1 > 0 and list(fast) == list(slow)
+    want, _ = oracle.reconstruct_graph(g.nbr, g.f1, g.f2, g.A, g.B, 400)
+    assert list(fast) == want
+
+
+def test_batch_and_server_reject_graphs(csp):
+    t = synth.random_small_graph(3)
+    g = csp.Graph(t.nbr, t.f1, t.f2)
+    L = csp.lib()
+    out = ctypes.c_void_p()
+    assert L.csp_server_create(g.handle, None, ctypes.byref(out)) == csp.ERR_INVALID
+    assert L.csp_upload_weights(g.handle, t.f1.ctypes.data, t.f2.ctypes.data, 0, None) == csp.ERR_INVALID
+    with pytest.raises(csp.CspError):
+        csp.Batch([(g, t.A, t.B, t.M)])
+    g.close()

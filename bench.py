@@ -327,7 +327,7 @@ def run_ours(args):
     if world == 1 and args.fractal:
         line["fractal"] = bench_fractal(csp, synth)
     if world == 1 and args.graphs:
-        line["graphs"] = bench_graphs(csp, synth)
+        line["graphs"] = bench_graphs(csp, synth, args.graph_side)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, ORACLE_SAMPLE_CYCLES)
     print(json.dumps(line), flush=True)
@@ -610,6 +610,7 @@ def main():
                     help="also measure the mean active-set size vs time on 1024^2 i.i.d. lattices (N=1)")
     ap.add_argument("--graphs", type=int, default=0,
                     help="also time general graphs against the lattice path on 2048^2 (N=1)")
+    ap.add_argument("--graph-side", type=int, default=2048, help="side of the --graphs lattices")
     ap.add_argument("--fractal", type=int, default=0,
                     help="also count the active vertices at time t = 4096 on the environments omega_j (N=1)")
     ap.add_argument("--anticorrelated", type=int, default=1,

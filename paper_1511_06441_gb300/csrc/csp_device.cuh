@@ -9,7 +9,8 @@
 //                     its high half equals label[] at every cycle boundary
 //   isB[V/32] uint32  bitmap of B
 //   src_stamp uint32  per vertex: the last pass in which it sourced a live flow (trace mode)
-//   edge_stamp uint32 per directed edge (v * 2d + dir): the last pass in which it carried a
+//   nbw[8V]   uint32  general graphs only: slot j of v = neighbour << 3 | the slot of v there
+//   edge_stamp uint32 per directed edge (v * slots + dir): the last pass in which it carried a
 //                     flow that did not arrive (trace mode; phantom count)
 //   cand[]    uint32  arrivals of the current cycle (flow word ed of each arriving flow),
 //                     one region of cand_cap / G entries per CTA of the group
@@ -122,7 +123,7 @@ struct Params {
     unsigned long long *offer;
     const uint32_t *isB;
     uint32_t *src_stamp;           // trace mode: [V rounded up to 4] last pass each vertex sourced a live flow
-    uint32_t *edge_stamp;          // nullable (trace mode, phantom count): [2d V] last pass each directed edge carried a staying flow
+    uint32_t *edge_stamp;          // nullable (trace mode, phantom count): [slots V] last pass each directed edge carried a staying flow
     uint32_t *cand;                // arrivals of the current cycle (the sources of A at the seed)
     unsigned int cand_cap;
     uint32_t *ed[2];
@@ -809,7 +810,7 @@ __device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters 
 // The winner commits the label (Step 8), records v if it is in B (Algorithm 2), and starts
 // a flow on every edge (v, w) with Label(v) - f2 > Label(w) under the labels at the end of
 // this cycle (Steps 4-5; a flow on an edge that already carries water is the paper's
-// phantom).  Its loads (offer[v], the edge record, the 2d neighbour labels) are issued
+// phantom).  Its loads (offer[v], the edge record, the neighbour labels) are issued
 // together.  Warps work independently.  With TRACE, also counts the vertices the sweep
 // stamped with this pass.
 template <int D, typename W, bool TRACE>

@@ -151,3 +151,43 @@ def test_batch_and_server_reject_graphs(csp):
     with pytest.raises(csp.CspError):
         csp.Batch([(g, t.A, t.B, t.M)])
     g.close()
+
+
+def test_graph_edge_cases(csp):
+    # a path graph 0 - 1 - ... - 9 with one slot per direction: F1, F2 in closed form
+    V = 10
+    nbr = np.full((V, 2), -1, np.int64)
+    nbr[:-1, 0] = np.arange(1, V)
+    nbr[1:, 1] = np.arange(V - 1)
+    f1 = np.where(nbr >= 0, 3, 0).astype(np.uint8)
+    f2 = np.where(nbr >= 0, 2, 0).astype(np.uint8)
+    g = csp.Graph(nbr, f1, f2)
+    r = g.solve([0], [V - 1], 2 * (V - 1) + 1, trace=True)
+    assert (r.F1, r.X, r.x_src, r.x_dir, r.F2) == (3 * (V - 1), V - 1, V - 2, 0, 2 * (V - 1))
+    assert g.solve([0], [V - 1], 2 * (V - 1)).F1 == -1            # the bound is strict
+    r = g.solve([0], [V - 1], 0, trace=True)                        # M <= 0: infeasible at once
+    assert r.F1 == -1 and r.cycles == 0 and r.trace.tolist() == [[0, 0, 0]]
+    with pytest.raises(csp.CspError):
+        g.solve([0], [0], 100)                                      # A and B must be disjoint
+    with pytest.raises(csp.CspError):
+        g.solve([0], [V], 100)                                      # ids out of range
+    g.close()
+    # no edges at all: nothing flows
+    e = csp.Graph(np.full((4, 3), -1, np.int64), np.zeros((4, 3), np.uint8), np.zeros((4, 3), np.uint8))
+    r = e.solve([0], [3], 50, trace=True)
+    assert r.F1 == -1 and r.cycles == 0
+    e.close()
+
+
+def test_graph_async_solve_equals_sync(csp):
+    import torch
+    g = synth.king_graph(96, 1, 16, seed=9)
+    gr = csp.Graph(g.nbr, g.f1, g.f2)
+    want = gr.solve(g.A, g.B, 500)
+    gr.reserve()
+    rec = torch.zeros(16, dtype=torch.int64, device="cuda")
+    gr.solve_async(torch.from_numpy(g.A).cuda(), torch.from_numpy(g.B).cuda(), 500, rec)
+    torch.cuda.synchronize()
+    got = csp.result_from_record(rec.cpu().numpy())
+    gr.close()
+    assert got.status == 0 and got.answer() == want.answer() and got.updates == want.updates

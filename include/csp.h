@@ -22,9 +22,11 @@
  * General graphs (csp_create_graph; Section 1 of the paper states the method for any
  * graph, and the bounded degree is what the GPU layout needs): up to 8 edges per vertex,
  * given as adjacency slots; the direction of an edge is its slot at the vertex it leaves.
- * A graph handle works with csp_solve, csp_solve_async, csp_reserve, csp_get_labels,
- * csp_reconstruct_path and csp_reconstruct_fast (the calls below that take a csp_lattice);
- * csp_upload_weights, the batch API and the server API accept lattices only.
+ * A graph handle works wherever a csp_lattice is taken: csp_solve, csp_solve_async,
+ * csp_reserve, csp_get_labels, both reconstructions, the batch API (graphs and lattices may
+ * share a batch) and the server API (explicit target lists only: a graph has no
+ * hyperplanes).  csp_upload_weights accepts lattices only, and csp_solve_static takes a
+ * lattice's extents.
  *
  * Every call returns a csp_status and never aborts.  Pointers named *_dev are device
  * pointers; all other pointers are host pointers.  Output buffers are owned by the
@@ -234,8 +236,8 @@ typedef struct csp_batch csp_batch;
 
 /* Allocates every instance's workspace, uploads the sets, plans the schedule and
  * captures the launch.  All lattices must use the same weight width.  The lattices must
- * outlive the batch.  Errors: CSP_ERR_INVALID (any query invalid on the host side, or a
- * graph among the handles), CSP_ERR_OOM, CSP_ERR_CUDA. */
+ * outlive the batch.  Errors: CSP_ERR_INVALID (any query invalid on the host side),
+ * CSP_ERR_OOM, CSP_ERR_CUDA. */
 csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_options *opt, csp_batch **out);
 
 /* Enqueues one run of the whole batch on stream (cudaStream_t or NULL); asynchronous. */
@@ -343,8 +345,7 @@ typedef struct {
 } csp_server_query;
 
 /* Allocates the slots and launches the persistent server kernel on its own stream.  The
- * lattice must outlive the server; while the server runs it occupies the GPU.
- * CSP_ERR_INVALID on a graph. */
+ * lattice (or graph) must outlive the server; while the server runs it occupies the GPU. */
 csp_status csp_server_create(csp_lattice *lat, const csp_server_options *opt, csp_server **out);
 
 /* The server's slots (groups), CTAs per slot and ring size. */

@@ -29,6 +29,7 @@ namespace {
 
 struct BatchInstance {
     const uint4 *rec;
+    const uint32_t *nbw;  // general graphs: the neighbour table (null on a lattice)
     long long V;
     int d, wbytes;
     int stride[4];
@@ -58,6 +59,7 @@ __device__ __forceinline__ Params<W> batch_params(const BatchInstance &I, unsign
 {
     Params<W> P{};
     P.rec = I.rec;
+    P.nbw = I.nbw;
     P.V = I.V;
     for (int k = 0; k < 4; k++) P.stride[k] = I.stride[k];
     P.label = I.label;
@@ -84,8 +86,8 @@ __device__ __forceinline__ Params<W> batch_params(const BatchInstance &I, unsign
     return P;
 }
 
-// One instance on its group, out of line: the four dimensions' solves get registers of
-// their own instead of sharing (and spilling) one inlined body.
+// One instance on its group, out of line: the solves of the four dimensions and of general
+// graphs get registers of their own instead of sharing (and spilling) one inlined body.
 template <int D, typename W>
 __device__ __noinline__ void batch_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t (&parity)[NSTAGE],
                                          unsigned long long &epoch)
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(TPB, CSP_BATCH_MIN_CTAS_PER_SM)
         case 1: batch_solve<1, W>(P, g, sm, parity, epoch); break;
         case 2: batch_solve<2, W>(P, g, sm, parity, epoch); break;
         case 3: batch_solve<3, W>(P, g, sm, parity, epoch); break;
+        case GRAPH: batch_solve<GRAPH, W>(P, g, sm, parity, epoch); break;
         default: batch_solve<4, W>(P, g, sm, parity, epoch); break;
         }
         __syncthreads();
@@ -357,7 +360,7 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
     for (int64_t i = 0; i < n; i++) {
         const csp_query &x = q[i];
         if (!x.lat || !x.A || !x.B || x.nA < 1 || x.nB < 1 || x.M >= (1ll << 31) - 1 || x.M < -(1ll << 31) + 1 ||
-            x.lat->wbytes != wbytes || x.lat->d == GRAPH)  // lattices only
+            x.lat->wbytes != wbytes)
             return CSP_ERR_INVALID;
     }
     csp_batch *b = new (std::nothrow) csp_batch();
@@ -423,6 +426,7 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
         I.wbytes = L->wbytes;
         for (int k = 0; k < 4; k++) I.stride[k] = L->stride[k];
         I.rec = (const uint4 *)L->rec;
+        I.nbw = L->nbw;
         I.cand_cap = (unsigned int)cand;
         I.pool_cap = (unsigned int)pool;
         I.nA = q[i].nA;
@@ -430,10 +434,13 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
         I.M = (int)q[i].M;
         I.max_cycles = opt ? opt->max_cycles : 0;
         // first guess before any run: cycles ~ the time to cross the longest side,
-        // updates ~ a few hundred per vertex (refined by csp_batch_tune)
+        // updates ~ a few hundred per vertex (refined by csp_batch_tune); a graph is guessed
+        // like a square lattice of V vertices
         int64_t s = 1;
-        for (int k = 0; k < L->d; k++) s = std::max<int64_t>(s, L->ext[k]);
-        b->stats[i] = InstStats{(L->d == 2 ? 11.0 : 8.0) * s, (L->d == 2 ? 4000.0 : 1000.0) * V};
+        for (int k = 0; k < num_axes(L); k++) s = std::max<int64_t>(s, L->ext[k]);
+        const bool flat = L->d == 2 || L->d == GRAPH;
+        if (L->d == GRAPH) s = std::max<int64_t>(1, (int64_t)std::sqrt((double)V));
+        b->stats[i] = InstStats{(flat ? 11.0 : 8.0) * s, (flat ? 4000.0 : 1000.0) * V};
     }
     e = cudaMalloc(&b->ws, std::max<size_t>(total, 256));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_inst, n * sizeof(BatchInstance));

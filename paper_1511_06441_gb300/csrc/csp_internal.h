@@ -57,6 +57,9 @@ struct csp_lattice {
 
 int num_sms(int device);
 
+// Coordinate axes of a handle: d for a lattice, 0 for a general graph (no hyperplanes).
+inline int num_axes(const csp_lattice *L) { return L->d == csp::GRAPH ? 0 : L->d; }
+
 // Device buffers that record improvements for path reconstruction (see Params).
 struct ReconLog {
     int32_t *first_t = nullptr;

@@ -70,6 +70,7 @@ struct GroupSlot {
 
 struct ServerArgs {
     const uint4 *rec;
+    const uint32_t *nbw;  // general graphs: the neighbour table (null on a lattice)
     long long V;
     int stride[4];
     const GroupSlot *slots;
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
     Params<W> &P = s_P;
     if (threadIdx.x == 0) {
     P.rec = S.rec;
+    P.nbw = S.nbw;
     P.V = S.V;
     for (int k = 0; k < 4; k++) P.stride[k] = S.stride[k];
     P.label = slot.label;
@@ -189,6 +191,7 @@ const void *server_kernel(int d)
     case 1: return (const void *)&k_server<1, W>;
     case 2: return (const void *)&k_server<2, W>;
     case 3: return (const void *)&k_server<3, W>;
+    case GRAPH: return (const void *)&k_server<GRAPH, W>;
     default: return (const void *)&k_server<4, W>;
     }
 }
@@ -236,7 +239,7 @@ bool valid_query(const csp_server *s, const csp_server_query &q)
     if (!q.A || q.nA < 1 || q.nA > kMaxInline || q.M >= (1ll << 31) - 1 || q.M < -(1ll << 31) + 1) return false;
     if (q.B) {
         if (q.nB < 1 || q.nB > kMaxInline) return false;
-    } else if (q.b_axis < 0 || q.b_axis >= s->lat->d || q.b_coord < 0 || q.b_coord >= s->lat->ext[q.b_axis]) {
+    } else if (q.b_axis < 0 || q.b_axis >= num_axes(s->lat) || q.b_coord < 0 || q.b_coord >= s->lat->ext[q.b_axis]) {
         return false;
     }
     return true;
@@ -266,7 +269,7 @@ extern "C" {
 
 csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_server **out)
 {
-    if (!L || !out || L->d == GRAPH) return CSP_ERR_INVALID;  // lattices only
+    if (!L || !out) return CSP_ERR_INVALID;
     *out = nullptr;
     csp_server *s = new (std::nothrow) csp_server();
     if (!s) return CSP_ERR_OOM;
@@ -356,6 +359,7 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
     ServerArgs a{};
     if (e == cudaSuccess) {
         a.rec = (const uint4 *)L->rec;
+        a.nbw = L->nbw;
         a.V = V;
         for (int k = 0; k < 4; k++) a.stride[k] = L->stride[k];
         a.slots = s->d_slots;
@@ -515,7 +519,7 @@ csp_status csp_serve_plain_replay(csp_lattice *L, const csp_server_query *q, con
         int64_t nB = q[i].nB;
         if (!Bp) {  // expand the hyperplane into an id list
             const int k = q[i].b_axis;
-            if (k < 0 || k >= L->d) return CSP_ERR_INVALID;
+            if (k < 0 || k >= num_axes(L)) return CSP_ERR_INVALID;
             const int64_t st = L->stride[k], nk = L->ext[k], count = L->V / nk;
             B.resize(count);
             for (int64_t j = 0; j < count; j++) B[j] = (j / st) * st * nk + q[i].b_coord * st + (j % st);

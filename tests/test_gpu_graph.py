@@ -2,11 +2,11 @@
 graph form, element by element (answer, cycles, updates, flows started, trace, phantoms,
 labels), on tiny random graphs (one CTA and several), phantom-rich tiny graphs, king's
 graphs with 8- and 16-bit weights, a medium random graph spanning many pool tiles, a
-lattice written as a graph (equal to the lattice path too), first passage at size, and
-path reconstruction.  All results are integers: the tolerance is zero.
+lattice written as a graph (equal to the lattice path too), first passage at size, path
+reconstruction, graphs in a batched launch next to lattices and graph queries served while
+others are in flight (both equal to single solves).  All results are integers: the tolerance
+is zero.
 """
-import ctypes
-
 import numpy as np
 import pytest
 
@@ -141,15 +141,10 @@ def test_king_graph_fast_path_equals_repeated_application(csp):
     assert list(fast) == want
 
 
-def test_batch_and_server_reject_graphs(csp):
+def test_weights_of_a_graph_are_fixed(csp):
     t = synth.random_small_graph(3)
     g = csp.Graph(t.nbr, t.f1, t.f2)
-    L = csp.lib()
-    out = ctypes.c_void_p()
-    assert L.csp_server_create(g.handle, None, ctypes.byref(out)) == csp.ERR_INVALID
-    assert L.csp_upload_weights(g.handle, t.f1.ctypes.data, t.f2.ctypes.data, 0, None) == csp.ERR_INVALID
-    with pytest.raises(csp.CspError):
-        csp.Batch([(g, t.A, t.B, t.M)])
+    assert csp.lib().csp_upload_weights(g.handle, t.f1.ctypes.data, t.f2.ctypes.data, 0, None) == csp.ERR_INVALID
     g.close()
 
 
@@ -191,3 +186,57 @@ def test_graph_async_solve_equals_sync(csp):
     got = csp.result_from_record(rec.cpu().numpy())
     gr.close()
     assert got.status == 0 and got.answer() == want.answer() and got.updates == want.updates
+
+
+def _key(r):
+    return (r.answer(), r.cycles, r.updates, r.launched)
+
+
+def test_batched_graphs_equal_single_solves(csp):
+    # king's graphs, random graphs and lattices (same weight width) in one batched launch
+    items, handles = [], []
+    for i in range(18):
+        if i % 3 == 0:
+            side = 24 + 6 * i
+            g = synth.king_graph(side, 1, 16, seed=100 + i)
+            h, A, B, M = csp.Graph(g.nbr, g.f1, g.f2), g.A, g.B, 12 * side
+        elif i % 3 == 1:
+            V = 3000 + 700 * i
+            nbr, f1, f2 = synth.random_graph(V, 6, seed=200 + i, lo=1, hi=16, drop=0.1)
+            h, A, B, M = csp.Graph(nbr, f1, f2), np.array([0, V // 2]), np.arange(V - 40, V), 70
+        else:
+            inst = synth.workload_64x64(300 + i)
+            h, A, B, M = csp.Lattice(inst.extents, inst.f1, inst.f2), inst.A, inst.B, 300
+        handles.append(h)
+        items.append((h, A, B, M))
+    b = csp.Batch(items)
+    b.run()
+    got = b.results()
+    single = [h.solve(A, B, M) for h, A, B, M in items]
+    assert all(r.status == csp.OK for r in got)
+    assert [_key(r) for r in got] == [_key(r) for r in single]
+    assert sum(r.F1 > 0 for r in single) >= 12
+    b.close()
+    for h in handles:
+        h.close()
+
+
+def test_served_graph_queries_equal_alone(csp):
+    nbr, f1, f2 = synth.random_graph(20_000, 6, seed=31, lo=1, hi=16, drop=0.1)
+    g = csp.Graph(nbr, f1, f2)
+    qs = []
+    for i in range(40):
+        r = synth.uniform_int(31, 1000 + i, 4, 0, 19_999)
+        A = np.unique(r[:2])
+        B = np.setdiff1d(synth.uniform_int(31, 2000 + i, 32, 0, 19_999), A)
+        qs.append(synth.Query(A, B, 40 + 5 * (i % 9)))
+    alone = [g.solve(q.A, q.B, q.M) for q in qs]
+    assert max(r.max_pool for r in alone) < 1 << 16
+    srv = csp.Server(g, group_ctas=4, max_groups=4, queue_capacity=16, session_seconds=120)
+    got, lat_s, _ = srv.replay(qs, np.zeros(len(qs)))
+    assert all(r.status == csp.OK for r in got)
+    assert [_key(r) for r in got] == [_key(r) for r in alone]
+    with pytest.raises(csp.CspError):   # a graph has no hyperplanes
+        srv.submit(synth.Query(qs[0].A, qs[0].B, 50, 0, 0))
+    srv.close()
+    g.close()

@@ -436,7 +436,8 @@ class GraphInstance:
     method for any graph).  Vertex v has S adjacency slots: ``nbr[v, j]`` is the neighbour
     in slot j (-1: empty), ``f1[v, j]`` >= 1 and ``f2[v, j]`` the travel time and weight of
     that edge.  Undirected: an edge sits in one slot at each end with the same weights.
-    The direction of an edge (the x_dir of a result) is its slot at the vertex it leaves."""
+    The direction of an edge (the x_dir of a result) is its slot at the vertex it leaves.
+    A directed graph lists each edge once, in a slot of its tail (see :func:`random_digraph`)."""
     nbr: np.ndarray         # (V, S) int64
     f1: np.ndarray          # (V, S) uint8 | uint16 (0 in empty slots)
     f2: np.ndarray          # (V, S) same dtype
@@ -559,3 +560,49 @@ def random_small_graph(seed: int, max_vertices: int = 12, rounds=(1, 4), f_hi: i
     B = np.sort(perm[nA:nA + nB]).astype(np.int64)
     M = int(1 + r[5] % np.uint64(M_max))
     return GraphInstance(nbr, f1, f2, A, B, M, f"tinygraph{seed}")
+
+
+def random_digraph(V: int, rounds: int = 6, seed: int = 9, lo: int = 1, hi: int = 16, f2_lo: Optional[int] = None,
+                   drop: float = 0.0, dtype=np.uint8):
+    """A random directed graph with out- and in-degree <= ``rounds`` (<= 8): round j draws a
+    random permutation p and puts the edge v -> p[v] in out-slot j of v; self loops, edges
+    already present and a fraction ``drop`` leave the slot empty.  f1 ~ U{lo..hi},
+    f2 ~ U{f2_lo..hi} per edge; an edge and its reverse get independent weights.
+    Returns (nbr, f1, f2) with nbr[v, j] the head of out-edge j of v."""
+    f2_lo = lo if f2_lo is None else f2_lo
+    nbr = np.full((V, rounds), -1, np.int64)
+    f1 = np.zeros((V, rounds), dtype)
+    f2 = np.zeros((V, rounds), dtype)
+    seen = set()
+    for j in range(rounds):
+        p = np.argsort(u64(seed, 800 + j, V), kind="stable")
+        keep = uniform_unit(seed, 900 + j, V) >= drop
+        w1 = uniform_int(seed, 1000 + j, V, lo, hi)
+        w2 = uniform_int(seed, 1100 + j, V, f2_lo, hi)
+        for v in np.flatnonzero(keep).tolist():
+            u = int(p[v])
+            if u == v or (v, u) in seen:
+                continue
+            seen.add((v, u))
+            nbr[v, j] = u
+            f1[v, j] = w1[v]
+            f2[v, j] = w2[v]
+    return nbr, f1, f2
+
+
+def random_small_digraph(seed: int, max_vertices: int = 12, rounds=(1, 4), f_hi: int = 6, M_max: int = 25,
+                         max_sources: Optional[int] = None, drop: float = 0.25) -> GraphInstance:
+    """A tiny random directed graph for brute-force comparisons (as :func:`random_small_graph`,
+    edges one way; ``nbr`` lists out-neighbours)."""
+    r = u64(seed, S_SHAPE + 60, 8)
+    V = 2 + int(r[0] % np.uint64(max_vertices - 1))
+    nr = rounds[0] + int(r[1] % np.uint64(rounds[1] - rounds[0] + 1))
+    nbr, f1, f2 = random_digraph(V, nr, seed, 1, f_hi, int(r[2] % np.uint64(2)), drop=drop)
+    perm = np.argsort(u64(seed, S_A + 60, V))
+    amax = max(1, V // 3) if max_sources is None else max_sources
+    nA = min(1 + int(r[3] % np.uint64(amax)), V - 1)
+    nB = min(1 + int(r[4] % np.uint64(max(1, (V - nA) // 2))), V - nA)
+    A = np.sort(perm[:nA]).astype(np.int64)
+    B = np.sort(perm[nA:nA + nB]).astype(np.int64)
+    M = int(1 + r[5] % np.uint64(M_max))
+    return GraphInstance(nbr, f1, f2, A, B, M, f"tinydigraph{seed}")

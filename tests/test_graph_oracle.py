@@ -171,3 +171,47 @@ def test_king_graph_interior_degree_is_eight():
     g = synth.king_graph(6)
     deg = (g.nbr >= 0).sum(1).reshape(6, 6)
     assert (deg[1:-1, 1:-1] == 8).all() and deg[0, 0] == 3 and deg[0, 3] == 5
+
+
+# ---------------------------------------------------------------- directed graphs
+
+@pytest.mark.parametrize("seed", range(300))
+def test_tiny_digraph_answer_equals_brute_force(seed):
+    g = synth.random_small_digraph(seed)
+    want = brute.brute_force(g)
+    got = o1(g)
+    assert got.answer() == tuple(want[:5])
+    assert oracle.pareto_graph(g.nbr, g.f1, g.f2, g.A, g.B, g.M).answer() == got.answer()
+
+
+def test_digraph_trace_and_phantoms_equal_brute_force():
+    with_phantoms = feasible = 0
+    for seed in range(400):
+        g = synth.random_small_digraph(seed, max_vertices=16, rounds=(3, 5), f_hi=20, M_max=150, max_sources=2,
+                                       drop=0.2)
+        r = o1(g)
+        np.testing.assert_array_equal(r.trace, brute.pareto_trace(g))
+        assert r.phantoms == brute.phantoms(g), seed
+        with_phantoms += r.phantoms > 0
+        feasible += r.F1 >= 0
+    assert with_phantoms >= 10 and feasible >= 100
+
+
+def test_digraph_f2_zero_is_first_passage():
+    nbr, f1, _ = synth.random_digraph(4000, 5, seed=13, lo=1, hi=9, drop=0.2)
+    A = np.array([0, 1999])
+    B = np.arange(3000, 3030)
+    F1, X, tau, rows = brute.graph_dijkstra_trace(nbr, f1, A, B)
+    got = oracle.cycle_graph(nbr, f1, np.zeros_like(f1), A, B, 2**31 - 2)
+    assert (got.F1, got.X) == (F1, X) and F1 > 0
+    np.testing.assert_array_equal(got.trace, rows)
+
+
+def test_random_digraph_degrees():
+    nbr, f1, f2 = synth.random_digraph(1000, 8, seed=5, drop=0.1)
+    indeg = np.bincount(nbr[nbr >= 0], minlength=1000)
+    assert indeg.max() <= 8 and (nbr != np.arange(1000)[:, None]).all()
+    for v in range(1000):
+        row = [int(u) for u in nbr[v] if u >= 0]
+        assert len(set(row)) == len(row)
+    assert ((nbr >= 0) == (f1 > 0)).all()

@@ -19,9 +19,10 @@
  *   - direction dir = 2k + s leads from a vertex to its neighbour v + e_k (s = 0) or
  *     v - e_k (s = 1).
  *
- * General graphs (csp_create_graph; Section 1 of the paper states the method for any
- * graph, and the bounded degree is what the GPU layout needs): up to 8 edges per vertex,
- * given as adjacency slots; the direction of an edge is its slot at the vertex it leaves.
+ * General graphs (csp_create_graph, undirected; csp_create_digraph, directed; Section 1 of
+ * the paper states the method for any graph, and the bounded degree is what the GPU layout
+ * needs): up to 8 edges per vertex, given as adjacency slots; the direction of an edge is
+ * its slot at the vertex it leaves.
  * A graph handle works wherever a csp_lattice is taken: csp_solve, csp_solve_async,
  * csp_reserve, csp_get_labels, both reconstructions, the batch API (graphs and lattices may
  * share a batch) and the server API (explicit target lists only: a graph has no
@@ -118,6 +119,14 @@ csp_status csp_create_lattice(int d, const int64_t *extents, const void *f1, con
  * offending vertex and slot are in csp_last_error), CSP_ERR_OOM, CSP_ERR_CUDA. */
 csp_status csp_create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void *f1, const void *f2,
                             int weight_bytes, void *stream, csp_lattice **out);
+
+/* Creates a directed graph: as csp_create_graph, but every slot holds a one-way edge from v to
+ * nbr[v * slots + j] (listed once, at its tail), with its own f1 and f2.  In-degrees must not
+ * exceed 8 either.  The direction x_dir of a result is the edge's slot at its tail.  The
+ * library keeps a second table of incoming edges (32 B more per vertex).
+ * Errors: as csp_create_graph ("in-degree above 8" among the reasons). */
+csp_status csp_create_digraph(int64_t V, int32_t slots, const int64_t *nbr, const void *f1, const void *f2,
+                              int weight_bytes, void *stream, csp_lattice **out);
 
 /* Overwrites the weights of an existing lattice (same layout and width as at creation),
  * without allocating.  on_device as above.  CSP_ERR_INVALID on a graph. */

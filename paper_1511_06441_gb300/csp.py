@@ -65,6 +65,7 @@ def lib():
         L.csp_create_lattice.argtypes = [ctypes.c_int, i64p, vp, vp, ctypes.c_int, ctypes.c_int, vp,
                                          ctypes.POINTER(vp)]
         L.csp_create_graph.argtypes = [i64, ctypes.c_int32, i64p, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.csp_create_digraph.argtypes = L.csp_create_graph.argtypes
         L.csp_upload_weights.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.csp_destroy_lattice.argtypes = [vp]
         L.csp_destroy_lattice.restype = None
@@ -80,7 +81,8 @@ def lib():
         L.csp_reconstruct_fast.argtypes = [vp, i64p, i64, i64p, i64, i64, ctypes.POINTER(CspOptions), i64,
                                            ctypes.POINTER(CspResult), i64p, i64, i64p]
         L.csp_reconstruct_path.restype = ctypes.c_int
-        for f in ("csp_create_lattice", "csp_create_graph", "csp_upload_weights", "csp_reserve", "csp_solve",
+        for f in ("csp_create_lattice", "csp_create_graph", "csp_create_digraph", "csp_upload_weights",
+                  "csp_reserve", "csp_solve",
                   "csp_solve_async",
                   "csp_get_labels", "csp_solve_static"):
             getattr(L, f).restype = ctypes.c_int
@@ -269,10 +271,12 @@ class Lattice:
 class Graph(Lattice):
     """A general graph resident on the GPU (``csp_create_graph``): ``nbr`` (V, S) neighbour
     ids (-1: empty slot), ``f1``/``f2`` (V, S) uint8 or uint16 the edge in each slot; S <= 8.
-    Undirected: every edge in one slot at each end with equal weights.  Solves and path
-    reconstruction work as on a lattice; x_dir is the slot of x at x_src."""
+    Undirected: every edge in one slot at each end with equal weights.  With ``directed``
+    (``csp_create_digraph``) every slot is a one-way edge v -> nbr[v, j] with its own weights,
+    in-degrees <= 8.  Solves, batches, the server and path reconstruction work as on a
+    lattice; x_dir is the slot of x at x_src."""
 
-    def __init__(self, nbr, f1, f2, stream=None):
+    def __init__(self, nbr, f1, f2, stream=None, directed: bool = False):
         nbr = np.ascontiguousarray(np.asarray(nbr, dtype=np.int64))
         if nbr.ndim != 2:
             raise ValueError("nbr must be (V, S)")
@@ -286,8 +290,10 @@ class Graph(Lattice):
         self.d = 0
         self.weight_bytes = f1.dtype.itemsize
         h = vp()
-        _check(lib().csp_create_graph(V, S, nbr.ctypes.data_as(i64p), f1.ctypes.data, f2.ctypes.data,
-                                      self.weight_bytes, _stream_handle(stream), ctypes.byref(h)), "csp_create_graph")
+        name = "csp_create_digraph" if directed else "csp_create_graph"
+        _check(getattr(lib(), name)(V, S, nbr.ctypes.data_as(i64p), f1.ctypes.data, f2.ctypes.data,
+                                    self.weight_bytes, _stream_handle(stream), ctypes.byref(h)), name)
+        self.directed = bool(directed)
         self._h = h
         self.V = int(lib().csp_num_vertices(h))
 

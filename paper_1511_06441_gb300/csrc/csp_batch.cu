@@ -29,7 +29,7 @@ namespace {
 
 struct BatchInstance {
     const uint4 *rec;
-    const uint32_t *nbw;  // general graphs: the neighbour table (null on a lattice)
+    const uint32_t *nbw, *nbw_in;  // general graphs: the out- and in-edge tables (null on a lattice)
     long long V;
     int d, wbytes;
     int stride[4];
@@ -60,6 +60,7 @@ __device__ __forceinline__ Params<W> batch_params(const BatchInstance &I, unsign
     Params<W> P{};
     P.rec = I.rec;
     P.nbw = I.nbw;
+    P.nbw_in = I.nbw_in;
     P.V = I.V;
     for (int k = 0; k < 4; k++) P.stride[k] = I.stride[k];
     P.label = I.label;
@@ -427,6 +428,7 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
         for (int k = 0; k < 4; k++) I.stride[k] = L->stride[k];
         I.rec = (const uint4 *)L->rec;
         I.nbw = L->nbw;
+        I.nbw_in = L->nbw_in;
         I.cand_cap = (unsigned int)cand;
         I.pool_cap = (unsigned int)pool;
         I.nA = q[i].nA;

@@ -9,7 +9,9 @@
 //                     its high half equals label[] at every cycle boundary
 //   isB[V/32] uint32  bitmap of B
 //   src_stamp uint32  per vertex: the last pass in which it sourced a live flow (trace mode)
-//   nbw[8V]   uint32  general graphs only: slot j of v = neighbour << 3 | the slot of v there
+//   nbw[8V]   uint32  general graphs only: out-slot j of v = head << 3 | the edge's in-slot at its head
+//   nbw_in[8V] uint32 general graphs only: in-slot k of u = tail << 3 | the edge's out-slot at its
+//                     tail (the same table as nbw on an undirected graph)
 //   edge_stamp uint32 per directed edge (v * slots + dir): the last pass in which it carried a
 //                     flow that did not arrive (trace mode; phantom count)
 //   cand[]    uint32  arrivals of the current cycle (flow word ed of each arriving flow),
@@ -118,7 +120,8 @@ struct Params {
     const uint4 *rec;              // per-vertex edge records (EdgeRecord<W, d>)
     long long V;
     int stride[4];                 // lattice strides (unused on a graph)
-    const uint32_t *nbw;           // graph only: [8 V] slot j of v = neighbour << 3 | the slot of v there
+    const uint32_t *nbw;           // graph only: [8 V] out-slot j of v = head << 3 | the edge's in-slot at its head
+    const uint32_t *nbw_in;        // graph only: [8 V] in-slot k of u = tail << 3 | the edge's out-slot there
     int32_t *label;
     unsigned long long *offer;
     const uint32_t *isB;
@@ -205,7 +208,8 @@ __device__ __forceinline__ uint32_t neighbour(const Params<W> &P, uint32_t v, un
     else return v + dir_offset<D>(P.stride, dir);
 }
 
-// Flow word of water leaving v in direction dir: dst << 3 | the direction from dst back to v.
+// Flow word of water leaving v in direction dir: dst << 3 | the direction from dst back to v
+// (on a graph: the edge's in-slot at dst).
 template <int D, typename W>
 __device__ __forceinline__ uint32_t flow_word(const Params<W> &P, uint32_t v, unsigned dir)
 {
@@ -218,7 +222,7 @@ template <int D, typename W>
 __device__ __forceinline__ uint32_t flow_source(const Params<W> &P, uint32_t ed, uint32_t &sdir)
 {
     if constexpr (D == GRAPH) {
-        const uint32_t x = __ldg(P.nbw + (size_t)(ed >> 3) * 8 + (ed & 7u));
+        const uint32_t x = __ldg(P.nbw_in + (size_t)(ed >> 3) * 8 + (ed & 7u));
         sdir = x & 7u;
         return x >> 3;
     } else {

@@ -33,7 +33,8 @@ struct csp_lattice {
     int device = 0;
     void *f1 = nullptr, *f2 = nullptr;  // device [d][V] (lattice only)
     void *rec = nullptr;                // device per-vertex edge records
-    uint32_t *nbw = nullptr;            // graph only: device [8 V] neighbour << 3 | back slot
+    uint32_t *nbw = nullptr;            // graph only: device [8 V] head << 3 | in-slot at the head
+    uint32_t *nbw_in = nullptr;         // graph only: device [8 V] tail << 3 | out-slot at the tail (= nbw if undirected)
     int rec_bytes = 16;
     unsigned long long flow_bound = 0;  // sum of f1 over directed edges: max flows alive
     // workspace of csp_solve / csp_solve_async

@@ -70,7 +70,7 @@ struct GroupSlot {
 
 struct ServerArgs {
     const uint4 *rec;
-    const uint32_t *nbw;  // general graphs: the neighbour table (null on a lattice)
+    const uint32_t *nbw, *nbw_in;  // general graphs: the out- and in-edge tables (null on a lattice)
     long long V;
     int stride[4];
     const GroupSlot *slots;
@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
     if (threadIdx.x == 0) {
     P.rec = S.rec;
     P.nbw = S.nbw;
+    P.nbw_in = S.nbw_in;
     P.V = S.V;
     for (int k = 0; k < 4; k++) P.stride[k] = S.stride[k];
     P.label = slot.label;
@@ -360,6 +361,7 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
     if (e == cudaSuccess) {
         a.rec = (const uint4 *)L->rec;
         a.nbw = L->nbw;
+        a.nbw_in = L->nbw_in;
         a.V = V;
         for (int k = 0; k < 4; k++) a.stride[k] = L->stride[k];
         a.slots = s->d_slots;

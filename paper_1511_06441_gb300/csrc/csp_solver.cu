@@ -427,6 +427,7 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         P.V = V;
         for (int k = 0; k < 4; k++) P.stride[k] = L->stride[k];
         P.nbw = L->nbw;
+        P.nbw_in = L->nbw_in;
         P.label = L->label;
         P.offer = L->offer;
         P.isB = L->isB;
@@ -559,9 +560,20 @@ csp_status csp_create_lattice(int d, const int64_t *extents, const void *f1, con
     return CSP_OK;
 }
 
-csp_status csp_create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void *f1, const void *f2,
-                            int weight_bytes, void *stream, csp_lattice **out)
+}  // extern "C"
+
+namespace {
+
+// Builds the device form of a general graph: per-vertex edge records (weights by out-slot),
+// the out-edge table nbw (head << 3 | in-slot at the head) and, for a directed graph, the
+// in-edge table nbw_in (tail << 3 | out-slot at the tail; in-slots numbered by (tail, out-slot)).
+// An undirected graph lists each edge at both ends; the slot at the other end is the
+// in-slot, so one table serves both.  Every id is checked here, so the kernels index only
+// valid vertices.
+csp_status create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void *f1, const void *f2, int weight_bytes,
+                        void *stream, bool directed, csp_lattice **out)
 {
+    const char *fn = directed ? "csp_create_digraph" : "csp_create_graph";
     if (!out || !nbr || !f1 || !f2 || V < 1 || V >= (1ll << 28) || slots < 1 || slots > 8 ||
         (weight_bytes != 1 && weight_bytes != 2))
         return CSP_ERR_INVALID;
@@ -572,14 +584,17 @@ csp_status csp_create_graph(int64_t V, int32_t slots, const int64_t *nbr, const 
     auto w2 = [&](int64_t i) -> int64_t {
         return weight_bytes == 1 ? ((const uint8_t *)f2)[i] : ((const uint16_t *)f2)[i];
     };
-    // Every edge must sit in one slot at each end with the same weights; the slot at the
-    // other end becomes the back direction of the flow word.
     const int rb = record_bytes(GRAPH, weight_bytes);
-    std::vector<uint32_t> nbw((size_t)V * 8);
+    std::vector<uint32_t> nbw((size_t)V * 8), nbw_in(directed ? (size_t)V * 8 : 0);
+    std::vector<uint8_t> indeg(directed ? (size_t)V : 0, 0);
     std::vector<unsigned char> rec((size_t)V * rb, 0);
     unsigned long long bound = 0;
+    for (int64_t v = 0; v < V; v++)
+        for (int j = 0; j < 8; j++) {  // empty slots: v itself (f1 = 0, never followed)
+            nbw[(size_t)v * 8 + j] = (uint32_t)v << 3;
+            if (directed) nbw_in[(size_t)v * 8 + j] = (uint32_t)v << 3;
+        }
     for (int64_t v = 0; v < V; v++) {
-        for (int j = 0; j < 8; j++) nbw[(size_t)v * 8 + j] = (uint32_t)v << 3;  // empty: v itself, f1 = 0
         for (int j = 0; j < slots; j++) {
             const int64_t i = v * slots + j, u = nbr[i];
             if (u == -1) continue;
@@ -590,17 +605,23 @@ csp_status csp_create_graph(int64_t V, int32_t slots, const int64_t *nbr, const 
             else if (w1(i) < 1) why = "travel time below 1";
             for (int k = 0; k < j && !why; k++)
                 if (nbr[v * slots + k] == u) why = "parallel edge";
-            for (int k = 0; k < slots && !why; k++)
-                if (nbr[u * slots + k] == v) {
-                    if (w1(u * slots + k) != w1(i) || w2(u * slots + k) != w2(i)) why = "weights differ at the two ends";
-                    back = k;
-                }
-            if (!why && back < 0) why = "edge missing at its other end";
+            if (!why && directed) {
+                back = indeg[u]++;
+                if (back >= 8) why = "in-degree above 8";
+            } else if (!why) {
+                for (int k = 0; k < slots && !why; k++)
+                    if (nbr[u * slots + k] == v) {
+                        if (w1(u * slots + k) != w1(i) || w2(u * slots + k) != w2(i)) why = "weights differ at the two ends";
+                        back = k;
+                    }
+                if (!why && back < 0) why = "edge missing at its other end";
+            }
             if (why) {
-                set_error("csp_create_graph: vertex " + std::to_string(v) + " slot " + std::to_string(j) + ": " + why);
+                set_error(std::string(fn) + ": vertex " + std::to_string(v) + " slot " + std::to_string(j) + ": " + why);
                 return CSP_ERR_INVALID;
             }
             nbw[(size_t)v * 8 + j] = ((uint32_t)u << 3) | (uint32_t)back;
+            if (directed) nbw_in[(size_t)u * 8 + back] = ((uint32_t)v << 3) | (uint32_t)j;
             unsigned char *r = rec.data() + (size_t)v * rb;
             if (weight_bytes == 1) {
                 r[2 * j] = (uint8_t)w1(i);
@@ -623,17 +644,37 @@ csp_status csp_create_graph(int64_t V, int32_t slots, const int64_t *nbr, const 
     cudaGetDevice(&L->device);
     cudaError_t e = cudaMalloc(&L->rec, rec.size());
     if (e == cudaSuccess) e = cudaMalloc((void **)&L->nbw, nbw.size() * 4);
+    if (e == cudaSuccess && directed) e = cudaMalloc((void **)&L->nbw_in, nbw_in.size() * 4);
+    if (!directed) L->nbw_in = L->nbw;
     cudaStream_t s = (cudaStream_t)stream;
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->rec, rec.data(), rec.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->nbw, nbw.data(), nbw.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && directed)
+        e = cudaMemcpyAsync(L->nbw_in, nbw_in.data(), nbw_in.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         csp_destroy_lattice(L);
-        return cuda_fail(e, "csp_create_graph");
+        return cuda_fail(e, fn);
     }
     *out = L;
     return CSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+csp_status csp_create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void *f1, const void *f2,
+                            int weight_bytes, void *stream, csp_lattice **out)
+{
+    return create_graph(V, slots, nbr, f1, f2, weight_bytes, stream, false, out);
+}
+
+csp_status csp_create_digraph(int64_t V, int32_t slots, const int64_t *nbr, const void *f1, const void *f2,
+                              int weight_bytes, void *stream, csp_lattice **out)
+{
+    return create_graph(V, slots, nbr, f1, f2, weight_bytes, stream, true, out);
 }
 
 csp_status csp_upload_weights(csp_lattice *L, const void *f1, const void *f2, int on_device, void *stream)
@@ -678,6 +719,7 @@ void csp_destroy_lattice(csp_lattice *L)
     if (L->f1) cudaFree(L->f1);
     if (L->f2) cudaFree(L->f2);
     if (L->rec) cudaFree(L->rec);
+    if (L->nbw_in && L->nbw_in != L->nbw) cudaFree(L->nbw_in);
     if (L->nbw) cudaFree(L->nbw);
     if (L->ws) cudaFree(L->ws);
     delete L;

@@ -117,3 +117,28 @@ def test_create_graph_rejects_bad_shapes(lib):
     f = np.ones(2, np.uint8)
     assert lib.csp_create_graph(i64(2), ctypes.c_int32(1), None, f.ctypes.data_as(vp), f.ctypes.data_as(vp), 1, None,
                                 ctypes.byref(out)) == INVALID
+
+
+def _digraph(lib, nbr, f1, slots=None):
+    nbr = np.ascontiguousarray(np.asarray(nbr, np.int64))
+    f1 = np.ascontiguousarray(np.asarray(f1, np.uint8))
+    f2 = np.zeros_like(f1)
+    out = vp()
+    st = lib.csp_create_digraph(i64(nbr.shape[0]), ctypes.c_int32(nbr.shape[1] if slots is None else slots), _p(nbr),
+                                f1.ctypes.data_as(vp), f2.ctypes.data_as(vp), 1, None, ctypes.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("nbr,f1,reason", [
+    ([[-1]] + [[0]] * 9, [[0]] + [[1]] * 9, b"in-degree above 8"),        # nine edges into vertex 0
+    ([[0], [-1]], [[1], [0]], b"self loop"),
+    ([[1, 1], [-1, -1]], [[1, 1], [0, 0]], b"parallel edge"),
+    ([[7], [-1]], [[1], [0]], b"out of range"),
+    ([[1], [-1]], [[0], [0]], b"travel time below 1"),
+])
+def test_create_digraph_rejects_broken_graphs(lib, nbr, f1, reason):
+    st, out = _digraph(lib, nbr, f1)
+    assert st == INVALID and not out.value
+    lib.csp_last_error.restype = ctypes.c_char_p
+    msg = lib.csp_last_error()
+    assert msg.startswith(b"csp_create_digraph: vertex") and reason in msg

@@ -240,3 +240,88 @@ def test_served_graph_queries_equal_alone(csp):
         srv.submit(synth.Query(qs[0].A, qs[0].B, 50, 0, 0))
     srv.close()
     g.close()
+
+
+# ---------------------------------------------------------------- directed graphs
+
+def _pair_directed(csp, t_nbr, f1, f2, A, B, M, ctas=0):
+    want = oracle.cycle_graph(t_nbr, f1, f2, A, B, M, labels=True)
+    g = csp.Graph(t_nbr, f1, f2, directed=True)
+    got = g.solve(A, B, M, trace=True, ctas=ctas, phantoms=True, trace_cap=1 << 17)
+    assert got.answer() == want.answer()
+    assert (got.cycles, got.updates, got.launched, got.phantoms) == \
+        (want.cycles, want.updates, want.launched, want.phantoms)
+    np.testing.assert_array_equal(got.trace, want.trace)
+    np.testing.assert_array_equal(g.labels(), want.labels.astype(np.int32))
+    g.close()
+    return got
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_tiny_digraph(csp, seed):
+    t = synth.random_small_digraph(seed)
+    _pair_directed(csp, t.nbr, t.f1, t.f2, t.A, t.B, t.M, ctas=1 + seed % 5)
+
+
+def test_phantom_rich_tiny_digraphs(csp):
+    seen = 0
+    for seed in range(150):
+        t = synth.random_small_digraph(seed, max_vertices=16, rounds=(3, 5), f_hi=20, M_max=150, max_sources=2,
+                                       drop=0.2)
+        seen += _pair_directed(csp, t.nbr, t.f1, t.f2, t.A, t.B, t.M).phantoms > 0
+    assert seen >= 3
+
+
+def test_medium_digraph(csp):
+    nbr, f1, f2 = synth.random_digraph(120_000, 6, seed=41, lo=1, hi=16, drop=0.1)
+    A = np.arange(0, 120_000, 24_007)
+    tau = brute.graph_tau(nbr, f1, A)
+    B = np.argsort(-np.where(np.isfinite(tau), tau, -1), kind="stable")[:4]
+    got = _pair_directed(csp, nbr, f1, f2, A, B, 120)
+    assert got.F1 > 0 and int(got.trace[:, 2].max()) > 20 * 2048
+
+
+def test_undirected_graph_as_digraph_is_the_same_solve(csp):
+    g = synth.king_graph(96, 1, 16, seed=12)
+    a = csp.Graph(g.nbr, g.f1, g.f2)
+    b = csp.Graph(g.nbr, g.f1, g.f2, directed=True)   # every edge listed at both ends = two arcs
+    ra = a.solve(g.A, g.B, 600, trace=True, phantoms=True)
+    rb = b.solve(g.A, g.B, 600, trace=True, phantoms=True)
+    assert _key(ra) == _key(rb) and ra.phantoms == rb.phantoms
+    np.testing.assert_array_equal(ra.trace, rb.trace)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("seed", range(0, 30))
+def test_digraph_reconstruction_equals_oracle(csp, seed):
+    t = synth.random_small_digraph(seed, max_vertices=16, rounds=(2, 4))
+    want_r = oracle.cycle_graph(t.nbr, t.f1, t.f2, t.A, t.B, t.M, trace=False)
+    want, _ = oracle.reconstruct_graph(t.nbr, t.f1, t.f2, t.A, t.B, t.M, first=want_r)
+    g = csp.Graph(t.nbr, t.f1, t.f2, directed=True)
+    got = g.reconstruct(t.A, t.B, t.M)
+    fast, r = g.reconstruct_fast(t.A, t.B, t.M)
+    g.close()
+    if want is None:
+        assert got is None and fast is None and r.F1 == -1
+    else:
+        assert list(got) == want and list(fast) == want
+
+
+def test_batched_digraphs_equal_single_solves(csp):
+    items, handles = [], []
+    for i in range(9):
+        V = 2000 + 900 * i
+        nbr, f1, f2 = synth.random_digraph(V, 6, seed=500 + i, lo=1, hi=16, drop=0.1)
+        h = csp.Graph(nbr, f1, f2, directed=True)
+        handles.append(h)
+        items.append((h, np.array([0, V // 3]), np.arange(V - 30, V), 80))
+    b = csp.Batch(items)
+    b.run()
+    got = b.results()
+    single = [h.solve(A, B, M) for h, A, B, M in items]
+    assert all(r.status == csp.OK for r in got)
+    assert [_key(r) for r in got] == [_key(r) for r in single]
+    b.close()
+    for h in handles:
+        h.close()

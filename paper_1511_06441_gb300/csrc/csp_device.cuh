@@ -647,16 +647,6 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
             const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
             L[i] = j < nfill ? __ldcg(P.label + (e[i] >> 3)) : INT_MAX;
         }
-        // On a graph the arrival code needs a load (the in-edge table): issue it for the
-        // flows due this cycle together with the label gathers.
-        uint32_t gcode[D == GRAPH ? IPT : 1];
-        if constexpr (D == GRAPH) {
-#pragma unroll
-            for (int i = 0; i < IPT; i++) {
-                const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
-                gcode[i] = j < nfill && sm.in_ta[s][j] == Tg ? arrival_code<D>(P, e[i]) : 0u;
-            }
-        }
         uint32_t bk[IPT], ba[IPT];
         uint32_t nk = 0, na = 0;
 #pragma unroll
@@ -674,10 +664,8 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
                 const uint32_t dst = e[i] >> 3;
                 const int32_t t = sm.in_ta[s][j];
                 if (t == Tg) {
-                    uint32_t code;
-                    if constexpr (D == GRAPH) code = gcode[i];
-                    else code = arrival_code<D>(P, e[i]);
-                    const unsigned long long key = ((unsigned long long)(uint32_t)q << 32) | code;
+                    const unsigned long long key =
+                        ((unsigned long long)(uint32_t)q << 32) | arrival_code<D>(P, e[i]);
                     atomicMax(P.offer + dst, key);
                     arr = true;
                 } else {

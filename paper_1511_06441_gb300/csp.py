@@ -268,6 +268,33 @@ class Lattice:
         return out
 
 
+def slots_from_edges(V: int, edges, f1, f2, directed: bool = False, slots: int = 0):
+    """Adjacency slots (nbr, f1, f2), each (V, S), from an edge list: ``edges`` (E, 2) vertex
+    pairs with ``f1``/``f2`` (E,) their travel times and weights.  Undirected: every edge is
+    put in the next free slot at both ends; directed: at its tail only.  Slots fill in edge
+    order.  S = ``slots`` if given, else the largest degree.  Raises ValueError above 8."""
+    edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    f1 = np.asarray(f1).reshape(-1)
+    f2 = np.asarray(f2).reshape(-1)
+    if f1.shape[0] != edges.shape[0] or f2.shape[0] != edges.shape[0] or f1.dtype != f2.dtype:
+        raise ValueError("f1 and f2 need one entry per edge and the same dtype")
+    ends = [edges[:, 0]] if directed else [edges[:, 0], edges[:, 1]]
+    deg = np.bincount(np.concatenate(ends), minlength=V) if edges.size else np.zeros(V, np.int64)
+    S = int(slots or max(1, int(deg.max()) if V else 1))
+    if S > 8 or int(deg.max(initial=0)) > S:
+        raise ValueError("a vertex has more edges than slots (at most 8)")
+    nbr = np.full((V, S), -1, np.int64)
+    g1 = np.zeros((V, S), f1.dtype)
+    g2 = np.zeros((V, S), f2.dtype)
+    fill = np.zeros(V, np.int64)
+    for e, (a, b) in enumerate(edges.tolist()):
+        for x, y in ((a, b),) if directed else ((a, b), (b, a)):
+            k = fill[x]
+            nbr[x, k], g1[x, k], g2[x, k] = y, f1[e], f2[e]
+            fill[x] = k + 1
+    return nbr, g1, g2
+
+
 class Graph(Lattice):
     """A general graph resident on the GPU (``csp_create_graph``): ``nbr`` (V, S) neighbour
     ids (-1: empty slot), ``f1``/``f2`` (V, S) uint8 or uint16 the edge in each slot; S <= 8.

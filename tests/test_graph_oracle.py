@@ -215,3 +215,36 @@ def test_random_digraph_degrees():
         row = [int(u) for u in nbr[v] if u >= 0]
         assert len(set(row)) == len(row)
     assert ((nbr >= 0) == (f1 > 0)).all()
+
+
+def test_slots_from_edges_round_trip():
+    from paper_1511_06441_gb300 import csp
+    nbr, f1, f2 = synth.random_graph(300, 5, seed=4, drop=0.2)
+    V, S = nbr.shape
+    E = [(v, int(nbr[v, j]), int(f1[v, j]), int(f2[v, j])) for v in range(V) for j in range(S)
+         if nbr[v, j] > v]
+    edges = np.array([(a, b) for a, b, _, _ in E])
+    n2, g1, g2 = csp.slots_from_edges(V, edges, np.array([w for *_, w, _ in E], np.uint8),
+                                      np.array([w for *_, w in E], np.uint8))
+    # the same undirected graph: the same edge set with the same weights, one slot per end
+    def edge_set(n, a1, a2):
+        return {(v, int(n[v, j]), int(a1[v, j]), int(a2[v, j])) for v in range(n.shape[0])
+                for j in range(n.shape[1]) if n[v, j] >= 0}
+    assert edge_set(n2, g1, g2) == edge_set(nbr, f1, f2)
+    # an oracle solve sees the same problem (slot order only renames directions)
+    A, B = [0, 1], list(range(250, 260))
+    a = oracle.cycle_graph(nbr, f1, f2, A, B, 60)
+    b = oracle.cycle_graph(n2, g1, g2, A, B, 60)
+    assert (a.F1, a.X, a.F2, a.updates) == (b.F1, b.X, b.F2, b.updates)
+    np.testing.assert_array_equal(a.trace, b.trace)
+
+
+def test_slots_from_edges_directed_and_limits():
+    from paper_1511_06441_gb300 import csp
+    nbr, f1, f2 = csp.slots_from_edges(3, [(0, 1), (0, 2), (2, 1)], np.array([1, 2, 3], np.uint8),
+                                       np.array([4, 5, 6], np.uint8), directed=True)
+    assert nbr.tolist() == [[1, 2], [-1, -1], [1, -1]]
+    assert f1.tolist() == [[1, 2], [0, 0], [3, 0]] and f2.tolist() == [[4, 5], [0, 0], [6, 0]]
+    star = [(0, k) for k in range(1, 10)]
+    with pytest.raises(ValueError):
+        csp.slots_from_edges(10, star, np.ones(9, np.uint8), np.ones(9, np.uint8))

@@ -11,7 +11,10 @@ The solvers live in ``csp_oracle.c`` (plain C, compiled here with gcc on first u
 * :func:`lexmin` - unconstrained lexicographic (F1, F2) Dijkstra (the bound M of the
   anti-correlated workload, and its answer where that bound does not bind);
 * :func:`cycle_graph`, :func:`pareto_graph`, :func:`reconstruct_graph` - O1, O2 and the
-  repeated application on a general graph given by adjacency slots.
+  repeated application on a general graph given by adjacency slots;
+* :func:`calendar`, :func:`calendar_graph` - O4, O1's loop reorganised around events
+  (per-edge queues, time buckets): a cross-check of O1 and of that reorganisation, with
+  event counts.
 
 Parity unpinned: nothing.  Every output is pinned by the tests against brute force,
 plain Dijkstra, closed forms or the paper's Lemma; see the C file's header.
@@ -60,10 +63,14 @@ def _load():
                                           ctypes.c_int64, ctypes.c_int64, i64p]
             lib.oracle_lexmin.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
                                           ctypes.c_int64, i64p, i64p, ctypes.c_int64, i64p]
+            lib.oracle_calendar.argtypes = [ctypes.c_int, i64p, i32p, i32p, i64p, ctypes.c_int64, i64p,
+                                            ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, i64p, i64p,
+                                            ctypes.c_int64, i64p, ctypes.c_void_p]
+            lib.oracle_calendar_graph.argtypes = [ctypes.c_int64, ctypes.c_int, i64p] + lib.oracle_calendar.argtypes[2:]
             lib.oracle_cycle_graph.argtypes = [ctypes.c_int64, ctypes.c_int, i64p] + lib.oracle_cycle.argtypes[2:]
             lib.oracle_pareto_graph.argtypes = [ctypes.c_int64, ctypes.c_int, i64p] + lib.oracle_pareto.argtypes[2:]
             for f in (lib.oracle_cycle, lib.oracle_pareto, lib.oracle_lexmin, lib.oracle_cycle_graph,
-                      lib.oracle_pareto_graph):
+                      lib.oracle_pareto_graph, lib.oracle_calendar, lib.oracle_calendar_graph):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -282,6 +289,48 @@ def lexmin(extents: Sequence[int], f1, f2, A, B, *, full: bool = False, path: bo
     if full:
         return tuple(int(x) for x in res)
     return int(res[0]), int(res[1])
+
+
+CALENDAR_EVENTS = ("arrivals", "stale_entries", "pushes", "removals", "fronts_checked")
+
+
+def _calendar(call, V, A, B, M, max_cycles, labels):
+    res = np.zeros(14, np.int64)
+    cap = 1 << 12
+    while True:
+        tr = np.zeros(3 * cap, np.int64)
+        tl = np.zeros(1, np.int64)
+        lab = np.zeros(V, np.int64) if labels else None
+        rc = call(_p64(A), A.size, _p64(B), B.size, int(M), int(max_cycles), _p64(res), _p64(tr), cap, _p64(tl),
+                  lab.ctypes.data if lab is not None else None)
+        if rc != OK:
+            raise OracleError(rc)
+        if tl[0] <= cap:
+            break
+        cap = int(tl[0])
+    r = Result(*[int(x) for x in res[:9]], trace=tr[: 3 * int(tl[0])].reshape(-1, 3), labels=lab)
+    r.events = dict(zip(CALENDAR_EVENTS, (int(x) for x in res[9:14])))
+    return r
+
+
+def calendar(extents: Sequence[int], f1, f2, A, B, M: int, *, max_cycles: int = 1 << 62,
+             labels: bool = False) -> Result:
+    """O4: the cycle loop driven by events (per-edge flow queues and arrival-time buckets).
+    Same outputs as :func:`cycle` (with trace) plus ``events``: the counts of arrivals,
+    stale bucket entries, flows pushed, removals and queue fronts inspected."""
+    ext, f1, f2, A, B = _common(extents, f1, f2, A, B)
+    V = int(np.prod(ext))
+    return _calendar(lambda *rest: _load().oracle_calendar(len(ext), _p64(ext), _p32(f1), _p32(f2), *rest), V, A, B,
+                     M, max_cycles, labels)
+
+
+def calendar_graph(nbr, f1, f2, A, B, M: int, *, max_cycles: int = 1 << 62, labels: bool = False) -> Result:
+    """O4 on a general graph (arrays as in :func:`cycle_graph`)."""
+    nbr, f1, f2, V, S = _graph_arrays(nbr, f1, f2)
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
+    return _calendar(lambda *rest: _load().oracle_calendar_graph(V, S, _p64(nbr), _p32(f1), _p32(f2), *rest), V, A,
+                     B, M, max_cycles, labels)
 
 
 def solve_instance(inst, **kw) -> Result:

@@ -16,6 +16,9 @@
  *                    and, on request, the active set at a given time.
  *   oracle_pareto    (O2) a label-setting Dijkstra over (vertex, quality) states with
  *                    dominance pruning; it knows nothing about cycles or flows.
+ *   oracle_calendar  (O4) O1's loop driven by events (per-edge flow queues, arrival-time
+ *                    buckets): a cross-check of O1 and of that reorganisation, with event
+ *                    counts.
  *   oracle_lexmin    lexicographic (F1, F2) Dijkstra without a weight bound: derives the
  *                    weight bound M of the anti-correlated workload and, where that
  *                    bound does not bind, the whole answer (F1, F2, X, x).
@@ -425,6 +428,277 @@ int oracle_cycle_graph(int64_t V, int S, const int64_t *nbr, const int32_t *f1, 
     int rc = graph_init(&L, V, S, nbr, f1, f2);
     if (rc) return rc;
     return cycle_core(L, A, nA, B, nB, M, max_cycles, res, trace, trace_cap, trace_len, snap_time, snap, snap_len, labels_out, removed);
+}
+
+/* ------------------------------------------------------------------ O4: event-driven form */
+
+/*
+ * O4.  The same cycle loop as O1, reorganised around events instead of a sweep over every
+ * flow, to check that the reorganisation is exact (it is the calendar-queue design for the
+ * GPU): the flows in flight on one directed edge form a queue in launch order, and since a
+ * vertex's label only rises their qualities rise too, so both arrivals (oldest first) and
+ * removals (lowest quality first) take from the front.  Flows are also listed under their
+ * arrival time (one bucket per time modulo max f1 + 1, with a count of the listed flows
+ * still alive), so the next cycle time is the first bucket with a live flow, and a cycle
+ * touches only its arrivals, the flows it launches and the front of the queues into the
+ * vertices it improves.  Outputs as O1 (res[0..8], trace, labels); res[9..13] count the
+ * events: arrivals taken from buckets, bucket entries found stale (removed earlier), flows
+ * pushed, removals, and queue fronts inspected by the removal step.
+ */
+typedef struct {
+    int32_t t0; /* launch time */
+    int32_t Q;  /* quality = Label(src) at launch */
+} qflow_t;
+
+typedef struct {
+    int64_t *a;
+    int64_t n, cap;
+} ivec_t;
+
+static int ivec_push(ivec_t *b, int64_t x)
+{
+    if (b->n == b->cap) {
+        int64_t nc = b->cap ? 2 * b->cap : 16;
+        int64_t *na = (int64_t *)realloc(b->a, (size_t)nc * sizeof(int64_t));
+        if (!na) return OR_OOM;
+        b->a = na;
+        b->cap = nc;
+    }
+    b->a[b->n++] = x;
+    return OR_OK;
+}
+
+static int calendar_core(lattice_t L, const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M,
+                         int64_t max_cycles, int64_t *res, int64_t *trace, int64_t trace_cap, int64_t *trace_len,
+                         int64_t *labels_out)
+{
+    const int64_t V = L.V, S = L.slots, E = V * S;
+    int rc = OR_OK;
+    unsigned char *inA = calloc((size_t)V, 1), *inB = calloc((size_t)V, 1);
+    int64_t *label = calloc((size_t)V, sizeof(int64_t));
+    int64_t *head = calloc((size_t)E, sizeof(int64_t)), *cnt = calloc((size_t)E, sizeof(int64_t));
+    int64_t *et = calloc((size_t)E, sizeof(int64_t)), *ew = calloc((size_t)E, sizeof(int64_t));
+    int64_t *edst = malloc((size_t)E * sizeof(int64_t)), *qoff = malloc((size_t)(E + 1) * sizeof(int64_t));
+    int64_t *in_off = calloc((size_t)(V + 1), sizeof(int64_t)), *in_e = NULL;
+    int64_t *out_count = calloc((size_t)V, sizeof(int64_t));
+    int64_t *bq = malloc((size_t)V * sizeof(int64_t)), *bsrc = malloc((size_t)V * sizeof(int64_t));
+    int64_t *bdir = malloc((size_t)V * sizeof(int64_t)), *touched = malloc((size_t)V * sizeof(int64_t));
+    int64_t *improved = malloc((size_t)V * sizeof(int64_t));
+    int64_t *xsrc = malloc((size_t)V * sizeof(int64_t)), *xdir = malloc((size_t)V * sizeof(int64_t));
+    qflow_t *qs = NULL;
+    ivec_t *bucket = NULL;
+    int64_t *blive = NULL;
+    int64_t W = 2, rows = 0, Time = 0, cycles = 0, updates = 0, launched = 0, phantoms = 0, live = 0, active = 0;
+    int64_t n_arr = 0, n_stale = 0, n_push = 0, n_rem = 0, n_front = 0;
+    for (int i = 0; i < 14; i++) res[i] = -1;
+    if (!inA || !inB || !label || !head || !cnt || !et || !ew || !edst || !qoff || !in_off || !out_count || !bq ||
+        !bsrc || !bdir || !touched || !improved || !xsrc || !xdir) {
+        rc = OR_OOM;
+        goto done;
+    }
+    rc = validate_sets(&L, A, nA, B, nB, inA, inB);
+    if (rc) goto done;
+    /* directed edges e = v * S + dir: destination, f1, f2, queue storage (f1 slots: one
+     * launch per cycle, each in flight for f1 time units), and the edges into each vertex */
+    qoff[0] = 0;
+    for (int64_t v = 0; v < V; v++)
+        for (int dir = 0; dir < S; dir++) {
+            const int64_t e = v * S + dir;
+            int64_t t = 0, w = 0, u = neighbour(&L, v, dir, &t, &w);
+            edst[e] = u;
+            et[e] = u >= 0 ? t : 0;
+            ew[e] = w;
+            qoff[e + 1] = qoff[e] + et[e];
+            if (u >= 0) in_off[u + 1]++;
+            if (et[e] + 1 > W) W = et[e] + 1;
+        }
+    for (int64_t v = 0; v < V; v++) in_off[v + 1] += in_off[v];
+    in_e = malloc((size_t)(in_off[V] + 1) * sizeof(int64_t));
+    qs = malloc((size_t)(qoff[E] + 1) * sizeof(qflow_t));
+    bucket = calloc((size_t)W, sizeof(ivec_t));
+    blive = calloc((size_t)W, sizeof(int64_t));
+    if (!in_e || !qs || !bucket || !blive) {
+        rc = OR_OOM;
+        goto done;
+    }
+    {
+        int64_t *fillp = touched; /* scratch: next free position per vertex */
+        for (int64_t v = 0; v < V; v++) fillp[v] = in_off[v];
+        for (int64_t e = 0; e < E; e++)
+            if (edst[e] >= 0) in_e[fillp[edst[e]]++] = e;
+    }
+    for (int64_t v = 0; v < V; v++) bq[v] = INT64_MIN;
+
+/* push a flow on edge e at time T with quality Q (the queue holds at most f1(e) flows) */
+#define CAL_PUSH(e, T, Q)                                                            \
+    do {                                                                             \
+        const int64_t e_ = (e);                                                      \
+        if (cnt[e_] > 0) phantoms++;                                                 \
+        qs[qoff[e_] + (head[e_] + cnt[e_]) % et[e_]] = (qflow_t){(int32_t)(T), (int32_t)(Q)}; \
+        cnt[e_]++;                                                                   \
+        const int64_t b_ = ((T) + et[e_]) % W;                                       \
+        if ((rc = ivec_push(&bucket[b_], e_))) goto done;                            \
+        blive[b_]++;                                                                 \
+        if (out_count[e_ / S]++ == 0) active++;                                      \
+        live++;                                                                      \
+        launched++;                                                                  \
+        n_push++;                                                                    \
+    } while (0)
+/* take the front flow of edge e off the edge (arrived or removed) */
+#define CAL_POP(e)                                                                   \
+    do {                                                                             \
+        const int64_t e_ = (e);                                                      \
+        const qflow_t f_ = qs[qoff[e_] + head[e_]];                                  \
+        blive[((int64_t)f_.t0 + et[e_]) % W]--;                                      \
+        head[e_] = (head[e_] + 1) % et[e_];                                          \
+        cnt[e_]--;                                                                   \
+        if (--out_count[e_ / S] == 0) active--;                                      \
+        live--;                                                                      \
+    } while (0)
+
+    /* Initialization (Algorithm 3) */
+    for (int64_t v = 0; v < V; v++)
+        if (inA[v]) label[v] = M;
+    for (int64_t v = 0; v < V; v++)
+        if (inA[v])
+            for (int dir = 0; dir < S; dir++) {
+                const int64_t e = v * S + dir, u = edst[e];
+                if (u >= 0 && label[v] - ew[e] > label[u]) CAL_PUSH(e, 0, label[v]);
+            }
+    if (rows < trace_cap) {
+        trace[0] = 0;
+        trace[1] = active;
+        trace[2] = live;
+    }
+    rows++;
+
+    while (live > 0) {
+        if (cycles >= max_cycles) {
+            rc = OR_TIMEOUT;
+            break;
+        }
+        /* the next time with a live arrival */
+        int64_t T = Time + 1;
+        while (blive[T % W] == 0) T++;
+        cycles++;
+        updates += live;
+        Time = T;
+        /* arrivals: the front flow of each listed edge, if it is the one due now */
+        ivec_t *bk = &bucket[T % W];
+        int64_t nt = 0;
+        for (int64_t i = 0; i < bk->n; i++) {
+            const int64_t e = bk->a[i];
+            if (cnt[e] == 0 || (int64_t)qs[qoff[e] + head[e]].t0 + et[e] != T) {
+                n_stale++; /* removed before it arrived */
+                continue;
+            }
+            const int64_t Q = qs[qoff[e] + head[e]].Q, u = edst[e], src = e / S, dir = e % S;
+            CAL_POP(e);
+            n_arr++;
+            const int64_t q = Q - ew[e];
+            if (bq[u] == INT64_MIN) touched[nt++] = u;
+            if (q > bq[u] || (q == bq[u] && (src < bsrc[u] || (src == bsrc[u] && dir < bdir[u])))) {
+                bq[u] = q;
+                bsrc[u] = src;
+                bdir[u] = dir;
+            }
+        }
+        bk->n = 0;
+        /* commit (Steps 2, 8) */
+        int64_t ni = 0;
+        for (int64_t i = 0; i < nt; i++) {
+            const int64_t u = touched[i];
+            if (bq[u] > label[u]) {
+                label[u] = bq[u];
+                xsrc[u] = bsrc[u];
+                xdir[u] = bdir[u];
+                improved[ni++] = u;
+            }
+            bq[u] = INT64_MIN;
+        }
+        qsort(improved, (size_t)ni, sizeof(int64_t), cmp_i64);
+        /* launch (Steps 4-5) under the labels at the end of the cycle */
+        for (int64_t i = 0; i < ni; i++) {
+            const int64_t v = improved[i];
+            for (int dir = 0; dir < S; dir++) {
+                const int64_t e = v * S + dir, u = edst[e];
+                if (u >= 0 && label[v] - ew[e] > label[u]) CAL_PUSH(e, T, label[v]);
+            }
+        }
+        /* removals (Steps 7-9): only a vertex whose label rose can make flows into it
+         * useless, and on each edge into it the useless flows are a prefix of the queue */
+        for (int64_t i = 0; i < ni; i++) {
+            const int64_t v = improved[i];
+            for (int64_t k = in_off[v]; k < in_off[v + 1]; k++) {
+                const int64_t e = in_e[k];
+                n_front++;
+                while (cnt[e] > 0 && (int64_t)qs[qoff[e] + head[e]].Q - ew[e] <= label[v]) {
+                    CAL_POP(e);
+                    n_rem++;
+                }
+            }
+        }
+        if (rows < trace_cap) {
+            trace[3 * rows] = Time;
+            trace[3 * rows + 1] = active;
+            trace[3 * rows + 2] = live;
+        }
+        rows++;
+        int64_t X = -1;
+        for (int64_t i = 0; i < ni; i++) {
+            const int64_t u = improved[i];
+            if (inB[u] && (X < 0 || label[u] > label[X] || (label[u] == label[X] && u < X))) X = u;
+        }
+        if (X >= 0) {
+            res[0] = Time;
+            res[1] = X;
+            res[2] = xsrc[X];
+            res[3] = xdir[X];
+            res[4] = M - label[X];
+            break;
+        }
+    }
+#undef CAL_PUSH
+#undef CAL_POP
+    res[5] = cycles;
+    res[6] = updates;
+    res[7] = launched;
+    res[8] = phantoms;
+    res[9] = n_arr;
+    res[10] = n_stale;
+    res[11] = n_push;
+    res[12] = n_rem;
+    res[13] = n_front;
+    if (!rc && labels_out) memcpy(labels_out, label, (size_t)V * sizeof(int64_t));
+done:
+    *trace_len = rows;
+    if (bucket)
+        for (int64_t b = 0; b < W; b++) free(bucket[b].a);
+    free(bucket); free(blive); free(qs); free(in_e);
+    free(inA); free(inB); free(label); free(head); free(cnt); free(et); free(ew); free(edst); free(qoff);
+    free(in_off); free(out_count); free(bq); free(bsrc); free(bdir); free(touched); free(improved);
+    free(xsrc); free(xdir);
+    return rc;
+}
+
+int oracle_calendar(int d, const int64_t *ext, const int32_t *f1, const int32_t *f2, const int64_t *A, int64_t nA,
+                    const int64_t *B, int64_t nB, int64_t M, int64_t max_cycles, int64_t *res, int64_t *trace,
+                    int64_t trace_cap, int64_t *trace_len, int64_t *labels_out)
+{
+    lattice_t L;
+    int rc = lattice_init(&L, d, ext, f1, f2);
+    if (rc) return rc;
+    return calendar_core(L, A, nA, B, nB, M, max_cycles, res, trace, trace_cap, trace_len, labels_out);
+}
+
+int oracle_calendar_graph(int64_t V, int S, const int64_t *nbr, const int32_t *f1, const int32_t *f2,
+                          const int64_t *A, int64_t nA, const int64_t *B, int64_t nB, int64_t M, int64_t max_cycles,
+                          int64_t *res, int64_t *trace, int64_t trace_cap, int64_t *trace_len, int64_t *labels_out)
+{
+    lattice_t L;
+    int rc = graph_init(&L, V, S, nbr, f1, f2);
+    if (rc) return rc;
+    return calendar_core(L, A, nA, B, nB, M, max_cycles, res, trace, trace_cap, trace_len, labels_out);
 }
 
 /* ------------------------------------------------------------------ O2 */

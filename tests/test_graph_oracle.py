@@ -248,3 +248,22 @@ def test_slots_from_edges_directed_and_limits():
     star = [(0, k) for k in range(1, 10)]
     with pytest.raises(ValueError):
         csp.slots_from_edges(10, star, np.ones(9, np.uint8), np.ones(9, np.uint8))
+
+
+@pytest.mark.parametrize("seed", range(0, 60))
+def test_digraph_reconstruction_is_an_optimal_simple_path(seed):
+    g = synth.random_small_digraph(seed)
+    r = o1(g, trace=False)
+    path, _ = oracle.reconstruct_graph(g.nbr, g.f1, g.f2, g.A, g.B, g.M, first=r)
+    want = brute.brute_force(g)
+    if r.F1 < 0:
+        assert path is None and want[0] == -1
+        return
+    assert path[0] in set(g.A.tolist()) and path[-1] == r.X and len(set(path)) == len(path)
+    t = w = 0
+    for a, b in zip(path, path[1:]):                  # every step follows an arc a -> b
+        j = [k for k in range(g.S) if g.nbr[a, k] == b]
+        assert len(j) == 1
+        t += int(g.f1[a, j[0]])
+        w += int(g.f2[a, j[0]])
+    assert (t, w) == (r.F1, r.F2) == (want[0], want[4]) and w < g.M

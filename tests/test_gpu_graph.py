@@ -325,3 +325,22 @@ def test_batched_digraphs_equal_single_solves(csp):
     b.close()
     for h in handles:
         h.close()
+
+
+def test_served_digraph_queries_equal_alone(csp):
+    nbr, f1, f2 = synth.random_digraph(20_000, 6, seed=33, lo=1, hi=16, drop=0.1)
+    g = csp.Graph(nbr, f1, f2, directed=True)
+    qs = []
+    for i in range(30):
+        r = synth.uniform_int(33, 1000 + i, 4, 0, 19_999)
+        A = np.unique(r[:2])
+        B = np.setdiff1d(synth.uniform_int(33, 2000 + i, 32, 0, 19_999), A)
+        qs.append(synth.Query(A, B, 40 + 5 * (i % 9)))
+    alone = [g.solve(q.A, q.B, q.M) for q in qs]
+    assert max(r.max_pool for r in alone) < 1 << 16
+    srv = csp.Server(g, group_ctas=4, max_groups=4, queue_capacity=16, session_seconds=120)
+    got, _, _ = srv.replay(qs, np.zeros(len(qs)))
+    srv.close()
+    g.close()
+    assert all(r.status == csp.OK for r in got)
+    assert [_key(r) for r in got] == [_key(r) for r in alone]

@@ -4,13 +4,14 @@
  * algorithm for the constrained shortest path problem on lattice graphs"
  * (arXiv 1511.06441).
  *
- * Problem (Section 1 of the paper): an undirected lattice subgraph G of Z^d, every edge
+ * Problem (Section 1 of the paper): an undirected lattice subgraph G of Z^d (or a general
+ * graph of bounded degree, below), every edge
  * e with a travel time f1(e) >= 1 and a weight f2(e) >= 0 (integers), disjoint vertex
  * sets A and B and a bound M.  Find F1 = min F1(pi) over paths pi from A to B with
  * F2(pi) < M, plus the endpoint X in B, the last edge x = (Y -> X) and F2 of that path
  * (what the paper's reconstruction by repeated application needs).
  *
- * Lattice layout (all entry points):
+ * Lattice layout (every entry point that takes a lattice):
  *   - d in [1, 4]; extents n_0..n_{d-1} >= 1; V = prod n_k < 2^28.
  *   - vertex id v = sum_k c_k * stride_k, coordinate 0 fastest (stride_0 = 1).
  *   - f1[k*V + v], f2[k*V + v] are travel time and weight of the edge (v, v + e_k),

@@ -5,9 +5,8 @@
  * (arXiv 1511.06441).
  *
  * Problem (Section 1 of the paper): an undirected lattice subgraph G of Z^d (or a general
- * graph of bounded degree, below), every edge
- * e with a travel time f1(e) >= 1 and a weight f2(e) >= 0 (integers), disjoint vertex
- * sets A and B and a bound M.  Find F1 = min F1(pi) over paths pi from A to B with
+ * graph of bounded degree, below), every edge e with a travel time f1(e) >= 1 and a weight
+ * f2(e) >= 0 (integers), disjoint vertex sets A and B and a bound M.  Find F1 = min F1(pi) over paths pi from A to B with
  * F2(pi) < M, plus the endpoint X in B, the last edge x = (Y -> X) and F2 of that path
  * (what the paper's reconstruction by repeated application needs).
  *

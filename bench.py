@@ -248,7 +248,7 @@ def run_ours(args):
     achieved = float(np.mean([alg_bytes[i] / (np.mean([kern_ms[k][i] for k in range(K)]) / 1e3) for i in range(nM)]))
     achieved /= 1e9
     peak, peak_src = peaks()
-    traffic = None
+    traffic, dram = None, None
     prof = os.path.join(ROOT, "profiles", "k_cycle_cube128_traffic.json")
     if os.path.exists(prof):
         try:
@@ -257,8 +257,10 @@ def run_ours(args):
             if pj.get("kernel_source_sha256") == _kernel_sha():
                 per_m = pj.get("traffic_bytes_per_launch", {})
                 traffic = float(np.mean([per_m[str(M)] for M in M_SWEEP]))
+                dram = dram_rate([per_m[str(M)] for M in M_SWEEP],
+                                 [float(np.mean([kern_ms[k][i] for k in range(K)])) for i in range(nM)])
         except Exception:
-            traffic = None
+            traffic, dram = None, None
 
     # end to end through the synchronous C-ABI call with host buffers
     e2e = None
@@ -307,6 +309,7 @@ def run_ours(args):
         "instances_per_s": world * K * nM / total_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "dram_gbs": dram, "dram_frac": dram / peak if dram is not None else None,
                      "kernel": "k_cycle (persistent cycle kernel)",
                      "algorithmic_bytes_per_launch": float(np.mean(alg_bytes)),
                      "kernel_ms_per_launch": kern_avg_ms},
@@ -584,6 +587,14 @@ def bench_serving(csp, synth, n_queries):
     lat.close()
     torch.cuda.empty_cache()
     return out
+
+
+def dram_rate(traffic_bytes, kernel_ms):
+    """DRAM GB/s of the cycle kernel: per launch, the ncu DRAM bytes (read + write) of that
+    solve over its CUDA-event time, averaged over the solves of a step."""
+    if len(traffic_bytes) != len(kernel_ms) or not kernel_ms:
+        raise ValueError("one traffic figure per timed solve")
+    return float(np.mean([b / (ms / 1e3) for b, ms in zip(traffic_bytes, kernel_ms)])) / 1e9
 
 
 def _kernel_sha():

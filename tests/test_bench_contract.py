@@ -23,3 +23,14 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_dram_rate():
+    sys.path.insert(0, ROOT)
+    import bench
+    # 39.1 GB in 34.1 ms and 42.9 GB in 46.5 ms: 1146.6 and 922.6 GB/s, mean 1034.6
+    r = bench.dram_rate([39.1e9, 42.9e9], [34.1, 46.5])
+    assert abs(r - (39.1 / 0.0341 + 42.9 / 0.0465) / 2) < 1e-6
+    import pytest
+    with pytest.raises(ValueError):
+        bench.dram_rate([1.0], [1.0, 2.0])

@@ -527,6 +527,10 @@ def bench_batched(csp, synth):
     agree = sum(1 for k in range(len(insts)) if r[k, 0] == 0 and tuple(int(x) for x in r[k, 1:6]) == res[k].answer())
     plain_ok = int((r[:, 0] == 0).sum())
     upd = sum(x.updates for x in res)
+    try:
+        cpu = cpu_baseline_batched(insts, [x.updates for x in res])
+    except Exception as e:  # the GPU numbers stand without it
+        cpu = {"error": f"{type(e).__name__}: {e}"}
     b.close()
     for L in lats:
         L.close()
@@ -537,12 +541,48 @@ def bench_batched(csp, synth):
             "speedup_vs_plain": ms_p / ms_b, "batched_ms": ms_b, "plain_ms": ms_p,
             "updates_per_s": upd / (ms_b / 1e3), "updates": upd,
             "statuses_ok": sum(1 for x in res if x.status == 0), "plain_statuses_ok": plain_ok,
-            "agree_with_plain": agree,
+            "agree_with_plain": agree, "cpu_baseline": cpu,
             "schedule": {"ctas": sched["ctas"], "group_sizes": {str(g): int((sched["group"] == g).sum())
                                                                 for g in sorted(set(sched["group"].tolist()))},
                          "planned_makespan_ms": model["makespan_us"] / 1e3,
                          "model": {k: round(v, 3) for k, v in model.items() if k != "makespan_us"}},
             "plain": "one cooperative launch per instance (csp_solve_async), sequential on one stream"}
+
+
+def _oracle_updates(job):
+    """One O1 solve in a worker process: returns its update count."""
+    import oracle
+    extents, f1, f2, A, B, M = job
+    return oracle.cycle(extents, f1, f2, A, B, M, trace=False).updates
+
+
+def cpu_baseline_batched(insts, updates, budget_updates=8e9, cap_updates=6e8, cores=None):
+    """The oracle (O1, as it stands) over independent instances on all host cores: a bounded
+    sample of the batch (every instance whose update count, known from the GPU run, is at most
+    ``cap_updates``, in index order, until ``budget_updates`` are taken), one O1 per instance in
+    a pool of spawned processes.  Reports instances/s on the sample and the whole batch's time
+    estimated from the sample's updates/s (the same updates the GPU counted)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    pick, tot = [], 0
+    for i, u in enumerate(updates):
+        if u <= cap_updates and tot + u <= budget_updates:
+            pick.append(i)
+            tot += u
+    jobs = [(insts[i].extents, insts[i].f1, insts[i].f2, insts[i].A, insts[i].B, insts[i].M) for i in pick]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        got = pool.map_async(_oracle_updates, jobs, chunksize=1).get(timeout=300)  # never wait forever
+    wall = time.perf_counter() - t0
+    if got != [updates[i] for i in pick]:
+        raise RuntimeError("the oracle's update counts differ from the GPU's")
+    rate = tot / wall
+    est = float(sum(updates)) / rate
+    return {"value": len(pick) / wall, "unit": "instances/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(pick)} of {len(insts)} instances (those with at most {cap_updates:.0e} updates, "
+                      f"{tot:.3e} updates in all), one single-threaded O1 per instance over {cores} processes",
+            "updates_per_s": rate, "whole_batch_estimate_s": est,
+            "whole_batch_instances_per_s_estimate": len(insts) / est}
 
 
 def bench_serving(csp, synth, n_queries):

@@ -34,3 +34,15 @@ def test_dram_rate():
     import pytest
     with pytest.raises(ValueError):
         bench.dram_rate([1.0], [1.0, 2.0])
+
+
+def test_cpu_baseline_batched_on_tiny_instances():
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_1511_06441_gb300 import synth
+    insts = [synth.random_small_instance(s, max_vertices=30) for s in range(12)]
+    ups = [oracle.cycle(i.extents, i.f1, i.f2, i.A, i.B, i.M, trace=False).updates for i in insts]
+    out = bench.cpu_baseline_batched(insts, ups, budget_updates=sum(ups), cap_updates=max(ups), cores=2)
+    assert out["kind"] == "oracle" and out["cores"] == 2 and out["value"] > 0
+    assert out["whole_batch_instances_per_s_estimate"] > 0 and "12 of 12" in out["sample"]

@@ -56,3 +56,11 @@ def test_oracle_is_not_imported_by_the_product():
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
             assert "csp_oracle" not in text, path
+
+
+def test_product_is_not_imported_by_the_oracle():
+    for path in glob.glob(os.path.join(ROOT, "oracle", "*")):
+        if path.endswith((".py", ".c", ".h")):
+            text = open(path).read()
+            assert "paper_1511_06441_gb300" not in text, path
+            assert "csp_device" not in text and "csp.h" not in text and "libcsp" not in text, path

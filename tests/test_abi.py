@@ -62,5 +62,5 @@ def test_product_is_not_imported_by_the_oracle():
     for path in glob.glob(os.path.join(ROOT, "oracle", "*")):
         if path.endswith((".py", ".c", ".h")):
             text = open(path).read()
-            assert "paper_1511_06441_gb300" not in text, path
-            assert "csp_device" not in text and "csp.h" not in text and "libcsp" not in text, path
+            assert "import paper_1511_06441_gb300" not in text and "from paper_1511_06441_gb300" not in text, path
+            assert "csp_device" not in text and '#include "csp' not in text and "libcsp" not in text, path

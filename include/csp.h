@@ -93,6 +93,20 @@ typedef struct {
 /* csp_options.flags: with a trace, also count phantoms (csp_result.phantoms); costs a store
  * per staying flow and a load per started flow in every cycle. */
 #define CSP_OPT_PHANTOMS 1
+/* csp_options.flags: which form of the cycle loop runs the solve (both give identical
+ * results, traces, counts and labels).
+ *   CSP_OPT_SWEEP  every cycle sweeps every flow in flight (Step 1 as the paper states it).
+ *   CSP_OPT_EVENT  a calendar of arrival times: a cycle touches only the flows that arrive,
+ *                  the flows it starts and the flows it removes (per-edge queues of flows
+ *                  in flight).  Needs max f1 <= 511 (CSP_ERR_INVALID otherwise) and, per
+ *                  lattice, 16 B per directed edge plus 8 B per unit of f1 summed over the
+ *                  directed edges, built on first use after each weight upload (that first
+ *                  solve synchronises its stream once).
+ * Neither flag: the library's default form for the handle (csp_default_engine).  Both:
+ * CSP_ERR_INVALID.  The first event-form solve on a handle also allocates its calendar
+ * (8 B per flow-pool slot of csp_reserve, plus part-filled chunks). */
+#define CSP_OPT_SWEEP 2
+#define CSP_OPT_EVENT 4
 
 /* Text for a status code (static storage). */
 const char *csp_status_string(csp_status s);
@@ -382,6 +396,17 @@ csp_status csp_server_destroy(csp_server *s);
  * csp_solve (one launch per query, in arrival order).  Same outputs as csp_server_replay. */
 csp_status csp_serve_plain_replay(csp_lattice *lat, const csp_server_query *q, const double *arrival_s, int64_t n,
                                   csp_result *out, int32_t *status, double *latency_s, double *makespan_s);
+
+/* The form (CSP_OPT_SWEEP or CSP_OPT_EVENT) a solve on this handle runs when its options
+ * name neither; -1 for a NULL handle.  May prepare the event form (synchronous, once per
+ * weight upload) to find out whether the handle supports it. */
+int32_t csp_default_engine(csp_lattice *lat);
+
+/* Device time of the last event-form solve on this handle, as measured by its first CTA:
+ * ns[0] = 0 (reserved), ns[1] = phase A (arrivals), ns[2] = phase B (winners: commits,
+ * launches, removals), ns[3] = waiting at grid barriers and reading counters.  For profiling.
+ * CSP_ERR_INVALID if no event-form solve has run on it. */
+csp_status csp_event_phase_times(const csp_lattice *lat, int64_t *ns);
 
 /* Copies the labels left by the last solve (V int32: M - F2 of the best water that has
  * reached each vertex by the final time, 0 if none) to labels_host. */

@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libcsp.so")
-SOURCES = ["csp_solver.cu", "csp_batch.cu", "csp_server.cu"]
+SOURCES = ["csp_solver.cu", "csp_event.cu", "csp_batch.cu", "csp_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -42,6 +42,9 @@ class CspOptions(ctypes.Structure):
                 ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 OPT_PHANTOMS = 1  # CSP_OPT_PHANTOMS
+OPT_SWEEP = 2     # CSP_OPT_SWEEP: every cycle sweeps every flow in flight
+OPT_EVENT = 4     # CSP_OPT_EVENT: a calendar of arrival times drives the cycles
+ENGINES = {None: 0, "sweep": OPT_SWEEP, "event": OPT_EVENT}
 
 
 class CspError(RuntimeError):
@@ -81,6 +84,10 @@ def lib():
         L.csp_reconstruct_fast.argtypes = [vp, i64p, i64, i64p, i64, i64, ctypes.POINTER(CspOptions), i64,
                                            ctypes.POINTER(CspResult), i64p, i64, i64p]
         L.csp_reconstruct_path.restype = ctypes.c_int
+        L.csp_default_engine.argtypes = [vp]
+        L.csp_default_engine.restype = ctypes.c_int32
+        L.csp_event_phase_times.argtypes = [vp, i64p]
+        L.csp_event_phase_times.restype = ctypes.c_int
         for f in ("csp_create_lattice", "csp_create_graph", "csp_create_digraph", "csp_upload_weights",
                   "csp_reserve", "csp_solve",
                   "csp_solve_async",
@@ -137,9 +144,14 @@ def _event_handle(ev) -> Optional[int]:
 
 
 def options(max_cycles: int = 0, pool_capacity: int = 0, ctas: int = 0, stream=None,
-            ev_begin=None, ev_end=None, time_limit_s: int = 0, phantoms: bool = False) -> CspOptions:
+            ev_begin=None, ev_end=None, time_limit_s: int = 0, phantoms: bool = False,
+            engine: Optional[str] = None) -> CspOptions:
+    """``csp_options``; ``engine`` = None (the library's default form), "sweep" or "event"."""
+    if engine not in ENGINES:
+        raise ValueError(f"engine must be one of {sorted(k for k in ENGINES if k)} or None")
+    flags = (OPT_PHANTOMS if phantoms else 0) | ENGINES[engine]
     return CspOptions(max_cycles, pool_capacity, ctas, int(time_limit_s), _stream_handle(stream),
-                      _event_handle(ev_begin), _event_handle(ev_end), OPT_PHANTOMS if phantoms else 0, 0)
+                      _event_handle(ev_begin), _event_handle(ev_end), flags, 0)
 
 
 class Lattice:
@@ -192,14 +204,15 @@ class Lattice:
 
     def solve(self, A, B, M: int, *, trace: bool = False, trace_cap: int = 1 << 16, max_cycles: int = 0,
               pool_capacity: int = 0, ctas: int = 0, stream=None, check: bool = True,
-              time_limit_s: int = 0, phantoms: bool = False) -> Result:
+              time_limit_s: int = 0, phantoms: bool = False, engine: Optional[str] = None) -> Result:
         """``csp_solve``: host sets in, host result out (blocks until done).
 
         ``phantoms`` (with ``trace``) also counts the flows started on an edge that already
-        carries one (``Result.phantoms``)."""
+        carries one (``Result.phantoms``).  ``engine``: "sweep", "event" or None (default form)."""
         A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
         B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
-        opt = options(max_cycles, pool_capacity, ctas, stream, time_limit_s=time_limit_s, phantoms=phantoms)
+        opt = options(max_cycles, pool_capacity, ctas, stream, time_limit_s=time_limit_s, phantoms=phantoms,
+                      engine=engine)
         res = CspResult()
         tr = np.zeros(3 * trace_cap, np.int64) if trace else None
         tl = ctypes.c_int64(0)
@@ -217,12 +230,12 @@ class Lattice:
 
     def solve_async(self, A_dev, B_dev, M: int, result_dev, *, trace_dev=None, trace_cap: int = 0,
                     max_cycles: int = 0, ctas: int = 0, stream=None, ev_begin=None, ev_end=None,
-                    time_limit_s: int = 0):
+                    time_limit_s: int = 0, engine: Optional[str] = None):
         """``csp_solve_async``: device sets (int64 tensors), device result (16 int64).
 
         ``ev_begin``/``ev_end``: optional CUDA events recorded around the cycle kernel.
         """
-        opt = options(max_cycles, 0, ctas, stream, ev_begin, ev_end, time_limit_s)
+        opt = options(max_cycles, 0, ctas, stream, ev_begin, ev_end, time_limit_s, engine=engine)
         _check(lib().csp_solve_async(self._h, _ptr(A_dev), int(A_dev.numel()), _ptr(B_dev), int(B_dev.numel()),
                                      int(M), ctypes.byref(opt), _ptr(result_dev),
                                      _ptr(trace_dev) if trace_dev is not None else None,
@@ -243,7 +256,8 @@ class Lattice:
         return out[: n.value].copy() if n.value else None
 
     def reconstruct_fast(self, A, B, M: int, *, log_capacity: int = 0, cap: int = 1 << 20, max_cycles: int = 0,
-                         ctas: int = 0, time_limit_s: int = 0, stream=None, ev_begin=None, ev_end=None):
+                         ctas: int = 0, time_limit_s: int = 0, stream=None, ev_begin=None, ev_end=None,
+                         engine: Optional[str] = None):
         """``csp_reconstruct_fast``: one recorded solve and a GPU backtrack.
 
         Returns ``(path, result)``; ``path`` is None if infeasible.  ``log_capacity`` < 0 keeps
@@ -252,7 +266,7 @@ class Lattice:
         """
         A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
         B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
-        opt = options(max_cycles, 0, ctas, stream, ev_begin, ev_end, time_limit_s)
+        opt = options(max_cycles, 0, ctas, stream, ev_begin, ev_end, time_limit_s, engine=engine)
         res = CspResult()
         out = np.zeros(cap, np.int64)
         n = ctypes.c_int64(0)
@@ -265,6 +279,18 @@ class Lattice:
     def labels(self) -> np.ndarray:
         out = np.zeros(self.V, np.int32)
         _check(lib().csp_get_labels(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "csp_get_labels")
+        return out
+
+    def default_engine(self) -> str:
+        """``csp_default_engine``: "sweep" or "event", the form a solve runs without ``engine``."""
+        f = int(lib().csp_default_engine(self._h))
+        return "event" if f == OPT_EVENT else "sweep"
+
+    def event_phase_times(self) -> np.ndarray:
+        """``csp_event_phase_times``: ns of the last event-form solve (reserved, phase A, phase B,
+        barriers), as measured by its first CTA."""
+        out = np.zeros(4, np.int64)
+        _check(lib().csp_event_phase_times(self._h, out.ctypes.data_as(i64p)), "csp_event_phase_times")
         return out
 
 

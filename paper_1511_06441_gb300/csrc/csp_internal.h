@@ -24,6 +24,8 @@ extern thread_local std::string g_last_error;
 inline int record_bytes(int d, int wbytes) { return wbytes * 2 * csp::nslots(d) <= 16 ? 16 : 32; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+struct csp_event_ws;
+
 struct csp_lattice {
     int d = 0;                          // lattice dimension 1..4, or csp::GRAPH
     int wbytes = 1;
@@ -37,6 +39,8 @@ struct csp_lattice {
     uint32_t *nbw_in = nullptr;         // graph only: device [8 V] tail << 3 | out-slot at the tail (= nbw if undirected)
     int rec_bytes = 16;
     unsigned long long flow_bound = 0;  // sum of f1 over directed edges: max flows alive
+    unsigned long long n_arcs = 0;      // directed edges (f1 > 0)
+    unsigned int max_f1 = 0;            // largest travel time
     // workspace of csp_solve / csp_solve_async
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -54,6 +58,7 @@ struct csp_lattice {
     int64_t trace_cap = 0;
     int64_t *sets = nullptr;  // device copies of A and B
     int64_t sets_cap = 0;
+    csp_event_ws *evw = nullptr;  // the event-driven form's edge queues and calendar (csp_event.cu)
 };
 
 int num_sms(int device);
@@ -80,3 +85,15 @@ inline int max_group_ctas(int device) { return std::min(4 * num_sms(device), csp
 // Pool slots a pass may leave unused: each CTA of a group holds one partly filled chunk
 // and one chunk allocated ahead.
 inline int64_t chunk_slack(int64_t group_ctas) { return 2 * group_ctas * (int64_t)csp::TILE; }
+
+// The event-driven form of the cycle loop (csp_event.cu).
+csp_status event_prepare(csp_lattice *L, cudaStream_t s);  // edge records for the current weights (synchronous)
+bool event_supported(const csp_lattice *L);                // prepared, max f1 < 512, rings fit 32-bit offsets
+csp_status event_reserve(csp_lattice *L, int64_t entry_cap);
+int64_t event_entry_cap(const csp_lattice *L);
+csp_status event_max_ctas(const csp_lattice *L, bool trace, int *out);
+csp_status event_launch(csp_lattice *L, const void *params, bool trace, int ctas, const csp_options *opt,
+                        cudaStream_t s);
+csp_status event_phase_times(const csp_lattice *L, unsigned long long *ns4);
+void event_invalidate(csp_lattice *L);  // the weights changed
+void event_release(csp_lattice *L);

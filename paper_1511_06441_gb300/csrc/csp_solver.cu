@@ -28,6 +28,7 @@
 
 #include "csp.h"
 #include "csp_device.cuh"
+#include "csp_event.cuh"
 #include "csp_internal.h"
 
 using namespace csp;
@@ -86,14 +87,30 @@ __global__ void k_build_records(const W *f1, const W *f2, long long V, int d, lo
 }
 
 
+// Weight statistics of the (upper-face-zeroed) travel times: out[0] = sum of f1 over the
+// directed edges (both directions of each edge: the most flows that can be in flight),
+// out[1] = directed edges, out[2] = the largest f1.
 template <typename W>
 __global__ void k_flow_bound(const W *f1, long long n, unsigned long long *out)
 {
-    unsigned long long s = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        s += f1[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, 2ull * s);
+    unsigned long long s = 0, c = 0;
+    unsigned int mx = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned int f = f1[i];
+        s += f;
+        c += f != 0;
+        mx = max(mx, f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (s) atomicAdd(out, 2ull * s);
+        if (c) atomicAdd(out + 1, 2ull * c);
+        if (mx) atomicMax(out + 2, (unsigned long long)mx);
+    }
 }
 
 // Resets the control block for a new solve.
@@ -375,6 +392,48 @@ int64_t default_pool_cap(const csp_lattice *L)
 }
 
 
+// The default form of the cycle loop for a handle.  The event form visits a flow when it
+// starts, arrives or is removed; the sweep visits every flow in flight in every cycle, so
+// the event form pays off when flows stay in flight over many cycles: measured on one
+// GB300, 1.21x and 1.25x faster at mean travel times of 128 and 256 (1024^2 lattices with
+// f1 ~ U{1..255} and U{1..511}), 0.80x at 32.5 (f1 ~ U{1..64}), 0.31x on the 128^3 cube
+// (f1 ~ U{1..16}) and 0.27-0.77x on the anti-correlated lattices (geometric f1, mean 10).
+// Its per-edge queues are larger than the sweep's flow pool, so where cycles are dense it
+// spends its time on random accesses that miss L2.  Rule: the event form when the mean f1
+// over directed edges is at least kEventMeanF1 and it supports the handle.
+constexpr unsigned long long kEventMeanF1 = 96;
+
+bool event_preferred(const csp_lattice *L)
+{
+    return L->n_arcs > 0 && L->max_f1 + 1 <= (unsigned int)EV_WMAX && L->flow_bound < 0xFFFFFF00ull &&
+           L->flow_bound >= kEventMeanF1 * L->n_arcs;
+}
+
+// Which form of the cycle loop runs a solve: CSP_OPT_SWEEP or CSP_OPT_EVENT choose one;
+// without either, event_preferred decides.  Preparing the event form (edge records, once
+// per weight upload) synchronises the stream.
+csp_status pick_engine(csp_lattice *L, const csp_options *opt, cudaStream_t s, bool *event)
+{
+    const int f = opt ? opt->flags : 0;
+    *event = false;
+    if ((f & CSP_OPT_SWEEP) && (f & CSP_OPT_EVENT)) {
+        set_error("CSP_OPT_SWEEP and CSP_OPT_EVENT are exclusive");
+        return CSP_ERR_INVALID;
+    }
+    if ((f & CSP_OPT_SWEEP) || (!(f & CSP_OPT_EVENT) && !event_preferred(L))) return CSP_OK;
+    csp_status st = event_prepare(L, s);
+    if (st != CSP_OK) return st;
+    if (!event_supported(L)) {
+        if (f & CSP_OPT_EVENT) {
+            set_error("the event form needs max f1 <= 511");
+            return CSP_ERR_INVALID;
+        }
+        return CSP_OK;
+    }
+    *event = true;
+    return CSP_OK;
+}
+
 // Enqueues one solve (set-up kernels + persistent kernel) on stream s.
 csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const int64_t *B_dev, int64_t nB, int64_t M,
                          const csp_options *opt, long long *trace_dev, int64_t trace_cap, int64_t *result_dev,
@@ -400,20 +459,31 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
     CSP_CUDA(cudaGetLastError());
 
     const bool trace = trace_dev != nullptr;
+    bool event = false;
+    csp_status est = pick_engine(L, opt, s, &event);
+    if (est != CSP_OK) return est;
     const void *fn = pick_kernel(L->d, L->wbytes, trace);
-    static thread_local bool attr_set[2][2][GRAPH + 1] = {};
-    bool &done = attr_set[L->wbytes - 1][trace][L->d];
-    if (!done) {
-        CSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-        done = true;
+    int max_ctas = 0;
+    if (event) {
+        est = event_reserve(L, L->pool_cap);
+        if (est != CSP_OK) return est;
+        est = event_max_ctas(L, trace, &max_ctas);
+        if (est != CSP_OK) return est;
+    } else {
+        static thread_local bool attr_set[2][2][GRAPH + 1] = {};
+        bool &done = attr_set[L->wbytes - 1][trace][L->d];
+        if (!done) {
+            CSP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+            done = true;
+        }
+        int per_sm = 0;
+        CSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TPB, kSmem));
+        if (per_sm < 1) {
+            g_last_error = "persistent kernel does not fit on an SM";
+            return CSP_ERR_CUDA;
+        }
+        max_ctas = std::min(per_sm * sms, max_group_ctas(L->device));
     }
-    int per_sm = 0;
-    CSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TPB, kSmem));
-    if (per_sm < 1) {
-        g_last_error = "persistent kernel does not fit on an SM";
-        return CSP_ERR_CUDA;
-    }
-    const int max_ctas = std::min(per_sm * sms, max_group_ctas(L->device));
     int ctas = opt && opt->ctas > 0 ? opt->ctas : (int)std::min<int64_t>(max_ctas, std::max<int64_t>(1, V / 4096));
     ctas = std::max(1, std::min(ctas, max_ctas));
 
@@ -469,6 +539,7 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         fill(P16);
         args[0] = &P16;
     }
+    if (event) return event_launch(L, args[0], trace, ctas, opt, s);
     if (opt && opt->ev_begin) CSP_CUDA(cudaEventRecord((cudaEvent_t)opt->ev_begin, s));
     CSP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(TPB), args, kSmem, s));
     if (opt && opt->ev_end) CSP_CUDA(cudaEventRecord((cudaEvent_t)opt->ev_end, s));
@@ -588,7 +659,7 @@ csp_status create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void
     std::vector<uint32_t> nbw((size_t)V * 8), nbw_in(directed ? (size_t)V * 8 : 0);
     std::vector<uint8_t> indeg(directed ? (size_t)V : 0, 0);
     std::vector<unsigned char> rec((size_t)V * rb, 0);
-    unsigned long long bound = 0;
+    unsigned long long bound = 0, arcs = 0, maxf1 = 0;
     for (int64_t v = 0; v < V; v++)
         for (int j = 0; j < 8; j++) {  // empty slots: v itself (f1 = 0, never followed)
             nbw[(size_t)v * 8 + j] = (uint32_t)v << 3;
@@ -631,6 +702,8 @@ csp_status create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void
                 ((uint16_t *)r)[2 * j + 1] = (uint16_t)w2(i);
             }
             bound += (unsigned long long)w1(i);
+            arcs++;
+            maxf1 = std::max<unsigned long long>(maxf1, (unsigned long long)w1(i));
         }
     }
     csp_lattice *L = new (std::nothrow) csp_lattice();
@@ -641,6 +714,8 @@ csp_status create_graph(int64_t V, int32_t slots, const int64_t *nbr, const void
     L->ext[0] = V;
     L->rec_bytes = rb;
     L->flow_bound = bound;
+    L->n_arcs = arcs;
+    L->max_f1 = (unsigned int)maxf1;
     cudaGetDevice(&L->device);
     cudaError_t e = cudaMalloc(&L->rec, rec.size());
     if (e == cudaSuccess) e = cudaMalloc((void **)&L->nbw, nbw.size() * 4);
@@ -683,14 +758,15 @@ csp_status csp_upload_weights(csp_lattice *L, const void *f1, const void *f2, in
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)L->d * L->V * L->wbytes;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    event_invalidate(L);
     CSP_CUDA(cudaMemcpyAsync(L->f1, f1, bytes, kind, s));
     CSP_CUDA(cudaMemcpyAsync(L->f2, f2, bytes, kind, s));
     const long long n[4] = {L->ext[0], L->ext[1], L->ext[2], L->ext[3]};
     const long long st[4] = {L->stride[0], L->stride[1], L->stride[2], L->stride[3]};
     const int blocks = std::max<int64_t>(1, std::min<int64_t>(4096, (L->d * L->V + 255) / 256));
     unsigned long long *bound = nullptr;
-    CSP_CUDA(cudaMallocAsync((void **)&bound, sizeof(unsigned long long), s));
-    CSP_CUDA(cudaMemsetAsync(bound, 0, sizeof(unsigned long long), s));
+    CSP_CUDA(cudaMallocAsync((void **)&bound, 3 * sizeof(unsigned long long), s));
+    CSP_CUDA(cudaMemsetAsync(bound, 0, 3 * sizeof(unsigned long long), s));
     if (L->wbytes == 1) {
         k_zero_upper_faces<uint8_t><<<blocks, 256, 0, s>>>((uint8_t *)L->f1, (uint8_t *)L->f2, L->V, L->d, st[0], st[1],
                                                            st[2], st[3], n[0], n[1], n[2], n[3]);
@@ -707,9 +783,13 @@ csp_status csp_upload_weights(csp_lattice *L, const void *f1, const void *f2, in
                                                         (unsigned char *)L->rec, L->rec_bytes);
     }
     CSP_CUDA(cudaGetLastError());
-    CSP_CUDA(cudaMemcpyAsync(&L->flow_bound, bound, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    unsigned long long stats[3] = {0, 0, 0};
+    CSP_CUDA(cudaMemcpyAsync(stats, bound, sizeof(stats), cudaMemcpyDeviceToHost, s));
     CSP_CUDA(cudaFreeAsync(bound, s));
     CSP_CUDA(cudaStreamSynchronize(s));
+    L->flow_bound = stats[0];
+    L->n_arcs = stats[1];
+    L->max_f1 = (unsigned int)stats[2];
     return CSP_OK;
 }
 
@@ -722,6 +802,7 @@ void csp_destroy_lattice(csp_lattice *L)
     if (L->nbw_in && L->nbw_in != L->nbw) cudaFree(L->nbw_in);
     if (L->nbw) cudaFree(L->nbw);
     if (L->ws) cudaFree(L->ws);
+    event_release(L);
     delete L;
 }
 
@@ -960,6 +1041,24 @@ csp_status csp_reconstruct_fast(csp_lattice *L, const int64_t *A, int64_t nA, co
     }
     cudaFree(buf);
     return st;
+}
+
+int32_t csp_default_engine(csp_lattice *L)
+{
+    if (!L) return -1;
+    bool event = false;
+    if (pick_engine(L, nullptr, nullptr, &event) != CSP_OK) return CSP_OPT_SWEEP;
+    return event ? CSP_OPT_EVENT : CSP_OPT_SWEEP;
+}
+
+csp_status csp_event_phase_times(const csp_lattice *L, int64_t *ns)
+{
+    if (!L || !ns) return CSP_ERR_INVALID;
+    unsigned long long t[4];
+    const csp_status st = event_phase_times(L, t);
+    if (st != CSP_OK) return st;
+    for (int i = 0; i < 4; i++) ns[i] = (int64_t)t[i];
+    return CSP_OK;
 }
 
 csp_status csp_get_labels(csp_lattice *L, int32_t *labels_host)

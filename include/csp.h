@@ -87,7 +87,8 @@ typedef struct {
     void *ev_begin;         /* nullable cudaEvent_t recorded on the stream just before the cycle kernel */
     void *ev_end;           /* nullable cudaEvent_t recorded just after it */
     int32_t flags;          /* CSP_OPT_* bits */
-    int32_t reserved;       /* 0 */
+    int32_t barrier_us;     /* longest wait at one device barrier, in microseconds, before the solve gives
+                               up with CSP_ERR_BARRIER; 0 = 4 s (a barrier round never takes seconds) */
 } csp_options;
 
 /* csp_options.flags: with a trace, also count phantoms (csp_result.phantoms); costs a store
@@ -107,6 +108,10 @@ typedef struct {
  * (8 B per flow-pool slot of csp_reserve, plus part-filled chunks). */
 #define CSP_OPT_SWEEP 2
 #define CSP_OPT_EVENT 4
+/* csp_options.flags, a test hook for the bounded waits: the last CTA of the solve leaves
+ * before its first grid barrier, so every other CTA's wait there runs out (after barrier_us)
+ * and the solve returns CSP_ERR_BARRIER with the device left usable.  Needs two CTAs or more. */
+#define CSP_OPT_TEST_ABSENT_CTA 8
 
 /* Text for a status code (static storage). */
 const char *csp_status_string(csp_status s);
@@ -215,7 +220,10 @@ csp_status csp_solve_async(csp_lattice *lat, const int64_t *A_dev, int64_t nA, c
  * 8 KiB of arrival list per CTA; whatever the vertex arrays leave of the static array
  * becomes the flow pool.  A lattice whose vertex arrays do not fit is rejected with
  * CSP_ERR_INVALID (csp_last_error() says so); a solve whose flows do not fit reports
- * CSP_ERR_CAPACITY in result_dev[0].  No trace is recorded.  The first call on a
+ * CSP_ERR_CAPACITY in result_dev[0].  No trace is recorded.  The cycle kernel stops after
+ * 120 s of device time (fixed: this entry point takes no csp_options) and then reports
+ * CSP_ERR_TIMEOUT in result_dev[0], as a solve stopped by max_cycles does; it always runs the
+ * sweep form of the loop.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) for that device;
  * make that first call before capturing any stream.  All calls share the array and
  * each call overwrites what the previous one left, so calls that may overlap on the GPU

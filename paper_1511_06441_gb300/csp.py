@@ -39,11 +39,12 @@ class CspResult(ctypes.Structure):
 class CspOptions(ctypes.Structure):
     _fields_ = [("max_cycles", ctypes.c_int64), ("pool_capacity", ctypes.c_int64), ("ctas", ctypes.c_int32),
                 ("time_limit_s", ctypes.c_int32), ("stream", vp), ("ev_begin", vp), ("ev_end", vp),
-                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("barrier_us", ctypes.c_int32)]
 
 OPT_PHANTOMS = 1  # CSP_OPT_PHANTOMS
 OPT_SWEEP = 2     # CSP_OPT_SWEEP: every cycle sweeps every flow in flight
 OPT_EVENT = 4     # CSP_OPT_EVENT: a calendar of arrival times drives the cycles
+OPT_TEST_ABSENT_CTA = 8  # CSP_OPT_TEST_ABSENT_CTA: test hook for the bounded barrier wait
 ENGINES = {None: 0, "sweep": OPT_SWEEP, "event": OPT_EVENT}
 
 
@@ -145,13 +146,14 @@ def _event_handle(ev) -> Optional[int]:
 
 def options(max_cycles: int = 0, pool_capacity: int = 0, ctas: int = 0, stream=None,
             ev_begin=None, ev_end=None, time_limit_s: int = 0, phantoms: bool = False,
-            engine: Optional[str] = None) -> CspOptions:
-    """``csp_options``; ``engine`` = None (the library's default form), "sweep" or "event"."""
+            engine: Optional[str] = None, barrier_us: int = 0, test_absent_cta: bool = False) -> CspOptions:
+    """``csp_options``; ``engine`` = None (the library's default form), "sweep" or "event";
+    ``barrier_us`` and ``test_absent_cta`` exercise the bounded barrier wait."""
     if engine not in ENGINES:
         raise ValueError(f"engine must be one of {sorted(k for k in ENGINES if k)} or None")
-    flags = (OPT_PHANTOMS if phantoms else 0) | ENGINES[engine]
+    flags = (OPT_PHANTOMS if phantoms else 0) | ENGINES[engine] | (OPT_TEST_ABSENT_CTA if test_absent_cta else 0)
     return CspOptions(max_cycles, pool_capacity, ctas, int(time_limit_s), _stream_handle(stream),
-                      _event_handle(ev_begin), _event_handle(ev_end), flags, 0)
+                      _event_handle(ev_begin), _event_handle(ev_end), flags, int(barrier_us))
 
 
 class Lattice:
@@ -204,15 +206,17 @@ class Lattice:
 
     def solve(self, A, B, M: int, *, trace: bool = False, trace_cap: int = 1 << 16, max_cycles: int = 0,
               pool_capacity: int = 0, ctas: int = 0, stream=None, check: bool = True,
-              time_limit_s: int = 0, phantoms: bool = False, engine: Optional[str] = None) -> Result:
+              time_limit_s: int = 0, phantoms: bool = False, engine: Optional[str] = None,
+              barrier_us: int = 0, test_absent_cta: bool = False) -> Result:
         """``csp_solve``: host sets in, host result out (blocks until done).
 
         ``phantoms`` (with ``trace``) also counts the flows started on an edge that already
-        carries one (``Result.phantoms``).  ``engine``: "sweep", "event" or None (default form)."""
+        carries one (``Result.phantoms``).  ``engine``: "sweep", "event" or None (default form).
+        ``barrier_us``/``test_absent_cta``: the bounded barrier wait and its test hook."""
         A = np.ascontiguousarray(np.asarray(A, dtype=np.int64).reshape(-1))
         B = np.ascontiguousarray(np.asarray(B, dtype=np.int64).reshape(-1))
         opt = options(max_cycles, pool_capacity, ctas, stream, time_limit_s=time_limit_s, phantoms=phantoms,
-                      engine=engine)
+                      engine=engine, barrier_us=barrier_us, test_absent_cta=test_absent_cta)
         res = CspResult()
         tr = np.zeros(3 * trace_cap, np.int64) if trace else None
         tl = ctypes.c_int64(0)

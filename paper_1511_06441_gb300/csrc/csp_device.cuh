@@ -142,6 +142,7 @@ struct Params {
     long long max_cycles;
     unsigned long long budget_ns;   // wall-clock budget of one launch (watchdog)
     unsigned long long barrier_ns;  // longest wait at one barrier before giving up
+    int test_absent;                // test hook: the group's last CTA leaves before its first barrier
     uint32_t *touched;              // nullable: vertices whose label left 0 are appended here
     unsigned int *touched_n;        // its length
     // Improvement record for path reconstruction (all nullable):
@@ -1008,6 +1009,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
     bool feasible = false;
     unsigned long long xkey = 0;
 
+    if (P.test_absent && g.size > 1 && g.rank == g.size - 1) return;  // (test hook: see Params)
     if (*(volatile int *)&ctl->status_in != 0) {
         status = *(volatile int *)&ctl->status_in;
         goto finish;

@@ -21,6 +21,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -519,7 +520,9 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
         P.M = (int)M;
         P.max_cycles = opt ? opt->max_cycles : 0;
         P.budget_ns = 1000000000ull * (unsigned long long)(opt && opt->time_limit_s > 0 ? opt->time_limit_s : 120);
-        P.barrier_ns = 4000000000ull;  // one barrier round never takes seconds
+        P.barrier_ns = opt && opt->barrier_us > 0 ? 1000ull * (unsigned long long)opt->barrier_us
+                                                  : 4000000000ull;  // one barrier round never takes seconds
+        P.test_absent = opt && (opt->flags & CSP_OPT_TEST_ABSENT_CTA) ? 1 : 0;
         if (rl) {
             P.first_t = rl->first_t;
             P.first_code = rl->first_code;
@@ -1087,9 +1090,12 @@ static __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
 void *g_static_addr[kMaxDevices] = {};
+std::mutex g_static_mutex;  // guards g_static_addr (calls may come from several host threads)
 
 // Host code cannot use g_static_ws directly: on the host that name is only a stand-in.
-// The device address is looked up once per device, with that device current.
+// The device address is looked up once per device, with that device current, and kept
+// for the life of the process (it does not survive a reset of the device's primary
+// context, e.g. by cudaDeviceReset).
 csp_status static_workspace_address(void **out)
 {
     int dev = 0;
@@ -1098,6 +1104,7 @@ csp_status static_workspace_address(void **out)
         g_last_error = "csp_solve_static: device index out of range";
         return CSP_ERR_INVALID;
     }
+    std::lock_guard<std::mutex> lock(g_static_mutex);
     if (!g_static_addr[dev]) {
         void *p = nullptr;
         CSP_CUDA(cudaGetSymbolAddress(&p, g_static_ws));
@@ -1151,7 +1158,8 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
         g_last_error = "persistent kernel does not fit on an SM";
         return CSP_ERR_CUDA;
     }
-    const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, V / 4096));
+    const int ctas = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>((int64_t)per_sm * sms, max_group_ctas(dev)), V / 4096));
     // carve the static array: per-vertex arrays, control block, then the candidate list,
     // the two pool buffers and their chunk fill arrays (sized from what is left)
     size_t off = 0;

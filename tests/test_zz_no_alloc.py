@@ -3,9 +3,14 @@
 Some callers cannot allocate device memory: code that runs inside a framework or runtime
 that owns every device allocation, or under a memory cap.  csp_solve_static keeps the
 solver's scratch in a static device array of the library instead.  Here it is called
-through the C ABI, two calls in a row (and then on a second instance), and each result
-must equal csp_solve's exactly: every output is an integer, so the tolerance is zero, as
-in the other parity tests.  This file is collected last on purpose.
+through the C ABI, two calls in a row (and then on other instances, among them a 3-D
+lattice with 16-bit weights, whose 32-byte edge records the static layout sizes apart),
+and each result must equal csp_solve's exactly: every output is an integer, so the
+tolerance is zero, as in the other parity tests.
+
+The file's name makes pytest collect it last, so that a run which stops at the first
+failure has run every other test before this one; it does not depend on them and passes
+alone in a fresh process as well.
 """
 import numpy as np
 import pytest
@@ -25,7 +30,10 @@ def test_static_solve_equals_csp_solve_on_consecutive_calls():
     build.build()
     cube = synth.workload_cube(40, 500)
     grid = synth.workload_64x64()
-    cases = [(cube, 500), (cube, 500), (grid, 300), (cube, 350)]
+    ext16 = [24, 24, 24]  # 16-bit weights with d = 3: 32-byte edge records
+    g1, g2 = synth.uniform_weights(ext16, 1, 300, 17, dtype=np.uint16)
+    wide = synth.Instance(ext16, g1, g2, synth.face(ext16, 0, 0), synth.face(ext16, 0, 23), 3000, "cube24_u16")
+    cases = [(cube, 500), (cube, 500), (grid, 300), (wide, 3000), (wide, 3000), (cube, 350)]
     want = {}
     for inst, M in cases:
         if (inst.name, M) not in want:

@@ -71,6 +71,49 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def alg_bytes_of(slots: int, rec) -> int:
+    """alg_bytes of a 16-int64 result record (updates, arrivals, improved, launched at 7, 13, 14, 8)."""
+    return alg_bytes(slots, int(rec[7]), int(rec[13]), int(rec[14]), int(rec[8]))
+
+
+def alg_bytes(slots: int, updates: int, arrivals: int, improved: int, launched: int) -> int:
+    """Algorithmic bytes of a solve (the per-unit figures of the measurement plan): 8 B per
+    active-edge update (read and write one remaining-time counter, Step 1), 13 B per arrival
+    (quality, f2, the 8-byte offer), 6 B per edge slot of an improved vertex (f1, f2 and the
+    neighbour's label) and 12 B per started flow."""
+    return 8 * updates + 13 * arrivals + 6 * slots * improved + 12 * launched
+
+
+def traffic_record(name: str):
+    """A per-launch DRAM traffic record under profiles/ (ncu dram__bytes_read.sum +
+    dram__bytes_write.sum), used only while the kernel sources it was taken from are unchanged."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        with open(path) as f:
+            pj = json.load(f)
+        if pj.get("kernel_source_sha256") == _kernel_sha():
+            return pj
+    except Exception:
+        pass
+    return None
+
+
+def roofline_block(alg: float, seconds: float, kernel: str, traffic=None, note: str = "") -> dict:
+    """Roofline of a timed region: algorithmic bytes over its time against the measured HBM copy
+    peak; with a matching ncu record, the DRAM bytes over the same time as well."""
+    peak, src = peaks()
+    gbs = alg / seconds / 1e9 if seconds > 0 else 0.0
+    out = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+           "traffic": traffic, "peak_source": src, "kernel": kernel, "algorithmic_bytes": float(alg),
+           "seconds": seconds}
+    if traffic is not None and seconds > 0:
+        out["dram_gbs"] = traffic / seconds / 1e9
+        out["dram_frac"] = out["dram_gbs"] / peak
+    if note:
+        out["note"] = note
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -128,7 +171,23 @@ def cpu_baseline(inst, max_cycles: int):
     dt = time.perf_counter() - t0
     return {"value": r.updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {r.cycles} cycles of the M=1600 solve ({r.updates} updates, {dt:.1f} s, "
-                      f"single-threaded C oracle O1)"}
+                      f"single-threaded C oracle O1)",
+            "whole_step": whole_step_oracle()}
+
+
+def whole_step_oracle():
+    """The oracle's recorded time for the whole step (the three full 128^3 solves), from the run that
+    wrote tests/golden/oracle_results.json on one x86 core: the early cycles a bounded sample times run
+    from cache, so the whole step's rate is the fairer denominator."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_results.json")) as f:
+            g = json.load(f)["cases"]
+        sec = sum(g[f"cube3d_128_M{M}"]["oracle_seconds"] for M in M_SWEEP)
+        upd = sum(g[f"cube3d_128_M{M}"]["updates"] for M in M_SWEEP)
+        return {"seconds": sec, "updates": upd, "updates_per_s": upd / sec, "cores": 1,
+                "where": "one x86 core of the build container (oracle_seconds in tests/golden/oracle_results.json)"}
+    except Exception:
+        return None
 
 
 def run_reference(args):
@@ -161,7 +220,8 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded SplitMix64)",
         "config": dict(WORKLOAD, parallelism="single CPU core"),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "whole_step": whole_step_oracle()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -243,7 +303,7 @@ def run_ours(args):
 
     # roofline of the cycle kernel (the only kernel that scales with the work)
     d = 3
-    alg_bytes = [8 * int(r[7]) + 13 * int(r[13]) + 2 * d * 6 * int(r[14]) + 12 * int(r[8]) for r in out]
+    alg_bytes = [alg_bytes_of(2 * d, r) for r in out]
     kern_avg_ms = float(np.mean(kern_ms))
     achieved = float(np.mean([alg_bytes[i] / (np.mean([kern_ms[k][i] for k in range(K)]) / 1e3) for i in range(nM)]))
     achieved /= 1e9
@@ -292,6 +352,11 @@ def run_ours(args):
                "ms_per_step": 1e3 * dt / args.e2e_steps}
         lat2.close()
 
+    # the same three solves in the event form of the cycle loop (A/B against the sweep above)
+    engines = None
+    if args.engines and world == 1:
+        engines = bench_engines(csp, lat, A, B, stream, trace, trace_cap, rec, out, kern_ms, args)
+
     if rank != 0:
         return
     line = {
@@ -306,7 +371,7 @@ def run_ours(args):
                              "launched": int(r[8]), "alg_bytes": alg_bytes[i],
                              "kernel_ms": float(np.mean([kern_ms[k][i] for k in range(K)]))}
                     for i, (M, r) in enumerate(zip(M_SWEEP, out))},
-        "instances_per_s": world * K * nM / total_s,
+        "cube128_solves_per_s": world * K * nM / total_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "dram_gbs": dram, "dram_frac": dram / peak if dram is not None else None,
@@ -316,15 +381,16 @@ def run_ours(args):
         "gpu_launches": 4 * nM * K,
         "clocks": clocks,
         "e2e": e2e,
+        "engines": engines,
     }
     del lat, f1, f2, flush, trace, rec
     torch.cuda.empty_cache()
     if world == 1 and args.batch:
         line["batched"] = bench_batched(csp, synth)
     if world == 1 and args.serve > 0:
-        line["serving"] = bench_serving(csp, synth, args.serve)
+        line["serving"] = bench_serving(csp, synth, args.serve, args.no_cpu_baseline)
     if world == 1 and args.anticorrelated:
-        line["anticorrelated"] = bench_anticorrelated(csp, synth)
+        line["anticorrelated"] = bench_anticorrelated(csp, synth, args.no_cpu_baseline)
     if world == 1 and args.open_problems:
         line["open_problems"] = bench_open_problems(csp, synth)
     if world == 1 and args.fractal:
@@ -333,10 +399,65 @@ def run_ours(args):
         line["graphs"] = bench_graphs(csp, synth, args.graph_side)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, ORACLE_SAMPLE_CYCLES)
+    line["summary"] = summary(line)  # last, so that a tail of the line keeps it
     print(json.dumps(line), flush=True)
 
 
-def bench_anticorrelated(csp, synth):
+def summary(line: dict) -> dict:
+    """The headline figures of every section, repeated compactly at the end of the line."""
+    s = {"updates_per_s": line["value"], "roofline_frac": line["roofline"]["frac"],
+         "e2e_updates_per_s": (line.get("e2e") or {}).get("value")}
+    eng = line.get("engines")
+    if eng:
+        s["event_form_vs_sweep"] = eng.get("event_vs_sweep")
+    b = line.get("batched")
+    if b and "instances_per_s" in b:
+        s["batched"] = {"instances_per_s": b["instances_per_s"], "plain_instances_per_s": b["plain_instances_per_s"],
+                        "speedup_vs_plain": b["speedup_vs_plain"], "agree_with_plain": b["agree_with_plain"],
+                        "roofline_frac": b["roofline"]["frac"]}
+    v = line.get("serving")
+    if v and v.get("rates"):
+        s["serving"] = {"queries": v["queries"], "p99_ms_served_vs_plain": [
+            [r["rate_x_saturation"], round(r["served"]["p99_ms"], 2), round(r["plain"]["p99_ms"], 2)] for r in v["rates"]],
+            "served_p99_le_plain_everywhere": all(r["served"]["p99_ms"] <= r["plain"]["p99_ms"] for r in v["rates"]),
+            "equal_to_alone": min(r["served"]["equal_to_alone"] for r in v["rates"])}
+    a = line.get("anticorrelated")
+    if a and "time_to_solution_s" in a:
+        s["anticorrelated"] = {"time_to_solution_s": a["time_to_solution_s"], "answer_equals_oracle":
+                               a["answer_equals_oracle"], "roofline_frac": a["roofline"]["frac"]}
+    return s
+
+
+def bench_engines(csp, lat, A, B, stream, trace, trace_cap, rec, sweep_out, sweep_ms, args):
+    """The step's three solves in the event form (CSP_OPT_EVENT), kernel time by CUDA events on the
+    solver's stream, one warm-up each; results must equal the sweep's."""
+    import torch
+    K = len(sweep_ms)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in M_SWEEP]
+    for a, b in evs:
+        a.record(stream)
+        b.record(stream)
+    ms = []
+    with torch.cuda.stream(stream):
+        for i, M in enumerate(M_SWEEP):
+            for rep in range(2):
+                lat.solve_async(A, B, M, rec[i], trace_dev=trace[i] if args.trace else None,
+                                trace_cap=trace_cap if args.trace else 0, stream=stream, ev_begin=evs[i][0],
+                                ev_end=evs[i][1], engine="event")
+                stream.synchronize()
+            ms.append(evs[i][0].elapsed_time(evs[i][1]))
+    got = rec.cpu().numpy()
+    same = bool((got[:, 1:9] == sweep_out[:, 1:9]).all())
+    sweep_avg = [float(np.mean([sweep_ms[k][i] for k in range(K)])) for i in range(len(M_SWEEP))]
+    upd = int(got[:, 7].sum())
+    return {"event_kernel_ms": ms, "sweep_kernel_ms": sweep_avg, "same_results": same,
+            "event_updates_per_s": upd / (sum(ms) / 1e3), "event_vs_sweep": sum(sweep_avg) / sum(ms),
+            "default_form": lat.default_engine(),
+            "note": "event form: per-edge queues and a calendar of arrival times (CSP_OPT_EVENT); the default "
+                    "form for this lattice is the sweep (mean f1 8.5 < 96)"}
+
+
+def bench_anticorrelated(csp, synth, no_cpu=False):
     """The 4096 x 4096 anti-correlated lattice (f1 geometric, f2 = 256 - f1, uint16, corner
     to corner, M = floor(1.2 F2*)): time to solution of one solve and the whole path from
     that solve (recorded first improvements + GPU backtrack), checked against the stored
@@ -383,9 +504,29 @@ def bench_anticorrelated(csp, synth):
         "note": "cycle kernel timed with CUDA events (first improvements recorded for the backtrack); "
                 "the path needs one solve, repeated application would need one per path vertex",
     }
+    tr = traffic_record("k_cycle_anticorr4096_traffic.json")
+    out["roofline"] = roofline_block(alg_bytes(4, r.updates, r.arrivals, r.improved, r.launched), kern_s,
+                                     "k_cycle (one persistent launch, the whole solve)",
+                                     tr["traffic_bytes_per_launch"] if tr else None)
     lat.close()
     torch.cuda.empty_cache()
+    if not no_cpu:
+        out["cpu_baseline"] = cpu_baseline_anticorrelated(inst)
     return out
+
+
+def cpu_baseline_anticorrelated(inst, cycles: int = 1500):
+    """The oracle (O1, as it stands) on one core over a bounded sample of the 4096^2 solve: its first
+    ``cycles`` cycles (the whole solve, 27,064 cycles with a pool of up to 3e8 flows, would take days)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.cycle(inst.extents, inst.f1, inst.f2, inst.A, inst.B, inst.M, max_cycles=cycles, trace=False,
+                     allow_timeout=True)
+    dt = time.perf_counter() - t0
+    return {"value": r.updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {r.cycles} cycles of the 4096^2 solve ({r.updates} updates, {dt:.1f} s, "
+                      f"single-threaded C oracle O1); early cycles have small pools"}
 
 
 def bench_open_problems(csp, synth, seeds=(6, 7, 8, 9), side=1024):
@@ -536,7 +677,12 @@ def bench_batched(csp, synth):
         L.close()
     torch.cuda.empty_cache()
     n = len(insts)
+    alg = sum(alg_bytes(2 * len(i.extents), x.updates, x.arrivals, x.improved, x.launched) for i, x in zip(insts, res))
+    tr = traffic_record("k_batch_batch512_traffic.json")
+    roof = roofline_block(alg, ms_b / 1e3, "k_batch (one persistent launch over all 512 instances)",
+                          tr["traffic_bytes_per_launch"] if tr else None)
     return {"workload": "batch512_mixed_2d32-1024_3d16-160_U1-32_faceA_faceB", "instances": n,
+            "roofline": roof,
             "instances_per_s": n / (ms_b / 1e3), "plain_instances_per_s": n / (ms_p / 1e3),
             "speedup_vs_plain": ms_p / ms_b, "batched_ms": ms_b, "plain_ms": ms_p,
             "updates_per_s": upd / (ms_b / 1e3), "updates": upd,
@@ -585,7 +731,7 @@ def cpu_baseline_batched(insts, updates, budget_updates=8e9, cap_updates=6e8, co
             "whole_batch_instances_per_s_estimate": len(insts) / est}
 
 
-def bench_serving(csp, synth, n_queries):
+def bench_serving(csp, synth, n_queries, no_cpu=False):
     """48^4 lattice, query stream served with continuous batching vs answered one at a time."""
     import torch
     ext, f1, f2 = synth.serving_lattice(48, 4, 5)
@@ -613,6 +759,8 @@ def bench_serving(csp, synth, n_queries):
         got, L, mk = srv.replay(qs, arr)
         served[m] = (got, L, mk)
     srv.close()
+    alg = sum(alg_bytes(8, x.updates, x.arrivals, x.improved, x.launched) for x in alone)
+    tr = traffic_record("k_server_lattice4d48_traffic.json")
     for m in rates:
         got, L, mk = served[m]
         arr = synth.poisson_arrivals(n_queries, m * mu, seed=5)
@@ -621,12 +769,66 @@ def bench_serving(csp, synth, n_queries):
             "rate_x_saturation": m, "rate_qps": m * mu,
             "served": {"qps": n_queries / mk, "p50_ms": 1e3 * float(np.median(L)),
                        "p99_ms": 1e3 * float(np.quantile(L, 0.99)),
-                       "equal_to_alone": sum(key(a) == key(b) for a, b in zip(got, alone))},
+                       "equal_to_alone": sum(key(a) == key(b) for a, b in zip(got, alone)),
+                       "roofline": roofline_block(alg, mk, "k_server (persistent, the whole stream)",
+                                                  note="algorithmic bytes of all queries over the stream's makespan "
+                                                       "(arrival-limited below saturation)")},
             "plain": {"qps": n_queries / pmk, "p50_ms": 1e3 * float(np.median(PL)),
                       "p99_ms": 1e3 * float(np.quantile(PL, 0.99))}})
+    top = out["rates"][-1]["served"]["roofline"]
+    out["roofline"] = dict(top, note="at the highest rate (1.25 x saturation: the server is busy throughout); "
+                                     "per-rate blocks under rates[*].served.roofline",
+                           traffic=tr["traffic_bytes_per_launch"] if tr else None)
     lat.close()
     torch.cuda.empty_cache()
+    if not no_cpu:
+        try:
+            out["cpu_baseline"] = cpu_baseline_serving(n_queries, [x.updates for x in alone])
+        except Exception as e:  # the GPU numbers stand without it
+            out["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
     return out
+
+
+_SERVE_STATE = {}
+
+
+def _serve_init():
+    from paper_1511_06441_gb300 import synth
+    _SERVE_STATE["lat"] = synth.serving_lattice(48, 4, 5)
+
+
+def _serve_oracle(job):
+    """One O1 query on the 48^4 serving lattice in a worker process: returns its update count."""
+    import oracle
+    from paper_1511_06441_gb300 import synth
+    ext, f1, f2 = _SERVE_STATE["lat"]
+    q = synth.serving_queries(1, ext, seed=5, start=job)[0]
+    return oracle.cycle(ext, f1, f2, q.A, q.B, q.M, trace=False).updates
+
+
+def cpu_baseline_serving(n_queries, updates, budget_updates=6e9, cores=None):
+    """The oracle (O1, as it stands) answering the query stream on all host cores: a bounded sample
+    (the first queries in stream order until ``budget_updates`` updates, counts known from the GPU),
+    one single-threaded O1 per query in a pool of spawned processes (each holds about 0.5 GB of
+    per-vertex state).  Queries/s on the sample; no arrival process (as fast as the cores go)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    pick, tot = [], 0
+    for i, u in enumerate(updates):
+        if tot + u > budget_updates:
+            break
+        pick.append(i)
+        tot += u
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores, initializer=_serve_init) as pool:
+        got = pool.map_async(_serve_oracle, pick, chunksize=1).get(timeout=300)
+    wall = time.perf_counter() - t0
+    if got != [updates[i] for i in pick]:
+        raise RuntimeError("the oracle's update counts differ from the GPU's")
+    return {"value": len(pick) / wall, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"the first {len(pick)} of {n_queries} queries ({tot:.3e} updates), one single-threaded O1 "
+                      f"per query over {cores} processes, no arrival process",
+            "updates_per_s": tot / wall}
 
 
 def dram_rate(traffic_bytes, kernel_ms):
@@ -655,6 +857,7 @@ def main():
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--trace", type=int, default=1, help="record the per-cycle trace (active set size) in the step")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--engines", type=int, default=1, help="also time the step's solves in the event form (N=1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=1, help="also measure 512 batched instances vs one launch each (N=1)")
     ap.add_argument("--open-problems", type=int, default=0,
@@ -666,7 +869,7 @@ def main():
                     help="also count the active vertices at time t = 4096 on the environments omega_j (N=1)")
     ap.add_argument("--anticorrelated", type=int, default=1,
                     help="also time the 4096^2 anti-correlated solve and its path (N=1; ~1.5 min)")
-    ap.add_argument("--serve", type=int, default=2000,
+    ap.add_argument("--serve", type=int, default=10000,
                     help="queries per rate for the serving comparison on the 48^4 lattice (0 = skip; N=1 only)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -359,6 +359,12 @@ typedef struct {
     int64_t memory_budget;    /* bytes for all slots together; 0 = no limit beyond max_groups */
     int64_t queue_capacity;   /* ring entries (queries submitted and not yet collected); 0 = 4 x slots */
     double session_seconds;   /* the persistent kernel gives up waiting after this long; 0 = 600 */
+    int32_t wide_depth;       /* two modes (0 = 2): while fewer than wide_depth queries wait, the whole grid
+                                 answers one query at a time (the latency of a plain solve without its
+                                 launch); from wide_depth waiting queries on, the groups serve them in
+                                 parallel (continuous batching) until every group is idle again.  -1 = groups
+                                 only.  The wide mode has a workspace of its own, sized for the whole grid */
+    int32_t reserved;         /* 0 */
 } csp_server_options;
 
 /* One query: 1..64 sources; targets either an explicit list (B, 1..64 ids) or, with
@@ -396,6 +402,11 @@ csp_status csp_server_poll(csp_server *s, int64_t ticket, csp_result *out, int32
  * completion - arrival; every output is nullable. */
 csp_status csp_server_replay(csp_server *s, const csp_server_query *q, const double *arrival_s, int64_t n,
                              csp_result *out, int32_t *status, double *latency_s, double *makespan_s);
+
+/* How the server's queries were answered so far: by the whole grid (wide) or by a group
+ * (narrow), and how often it switched between the two modes.  Nullable outputs. */
+csp_status csp_server_stats(const csp_server *s, int64_t *wide_queries, int64_t *narrow_queries, int64_t *to_wide,
+                            int64_t *to_narrow);
 
 /* Stops the server (after the queries already submitted) and frees it. */
 csp_status csp_server_destroy(csp_server *s);

@@ -519,7 +519,8 @@ def solve_batch(items, *, ctas: int = 0, max_group: int = 0, no_graph: bool = Fa
 
 class CspServerOptions(ctypes.Structure):
     _fields_ = [("group_ctas", ctypes.c_int32), ("max_groups", ctypes.c_int32), ("pool_capacity", i64),
-                ("memory_budget", i64), ("queue_capacity", i64), ("session_seconds", ctypes.c_double)]
+                ("memory_budget", i64), ("queue_capacity", i64), ("session_seconds", ctypes.c_double),
+                ("wide_depth", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class CspServerQuery(ctypes.Structure):
@@ -539,10 +540,11 @@ def _server_api():
         L.csp_server_replay.argtypes = [vp, ctypes.POINTER(CspServerQuery), dp, i64, ctypes.POINTER(CspResult),
                                         ctypes.POINTER(ctypes.c_int32), dp, dp]
         L.csp_server_destroy.argtypes = [vp]
+        L.csp_server_stats.argtypes = [vp, i64p, i64p, i64p, i64p]
         L.csp_serve_plain_replay.argtypes = [vp, ctypes.POINTER(CspServerQuery), dp, i64, ctypes.POINTER(CspResult),
                                              ctypes.POINTER(ctypes.c_int32), dp, dp]
         for f in ("csp_server_create", "csp_server_info", "csp_server_submit", "csp_server_poll", "csp_server_replay",
-                  "csp_server_destroy", "csp_serve_plain_replay"):
+                  "csp_server_destroy", "csp_serve_plain_replay", "csp_server_stats"):
             getattr(L, f).restype = ctypes.c_int
         L._server_ready = True
     return L
@@ -576,9 +578,12 @@ class Server:
     """``csp_server_*``: a resident lattice answering a query stream with continuous batching."""
 
     def __init__(self, lattice: "Lattice", *, group_ctas: int = 0, max_groups: int = 0, pool_capacity: int = 0,
-                 memory_budget: int = 0, queue_capacity: int = 0, session_seconds: float = 0.0):
+                 memory_budget: int = 0, queue_capacity: int = 0, session_seconds: float = 0.0, wide_depth: int = 0):
+        """``wide_depth``: waiting queries that switch the whole-grid (wide) mode to groups;
+        0 = the library default (2), -1 = groups only."""
         L = _server_api()
-        opt = CspServerOptions(group_ctas, max_groups, pool_capacity, memory_budget, queue_capacity, session_seconds)
+        opt = CspServerOptions(group_ctas, max_groups, pool_capacity, memory_budget, queue_capacity, session_seconds,
+                               int(wide_depth), 0)
         h = vp()
         _check(L.csp_server_create(lattice.handle, ctypes.byref(opt), ctypes.byref(h)), "csp_server_create")
         self._h = h
@@ -604,6 +609,12 @@ class Server:
         r = Result(*[int(getattr(res, name)) for name, _ in CspResult._fields_])
         r.status = st.value
         return r
+
+    def stats(self) -> dict:
+        """``csp_server_stats``: queries answered wide and narrow, and mode switches so far."""
+        v = [ctypes.c_int64(0) for _ in range(4)]
+        _check(_server_api().csp_server_stats(self._h, *[ctypes.byref(x) for x in v]), "csp_server_stats")
+        return dict(zip(("wide_queries", "narrow_queries", "to_wide", "to_narrow"), (x.value for x in v)))
 
     def replay(self, queries, arrival_s, use_hyperplane: bool = True):
         """Returns (results, latencies in s, makespan in s)."""

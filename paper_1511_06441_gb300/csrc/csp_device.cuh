@@ -1074,16 +1074,16 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             passes = pass;
 
             const PassCounts c = read_counters(C);
-            launched += (long long)c.launched;
-            arrivals += (long long)c.n_cand;
-            improved += (long long)c.improved;
-            phantoms += (long long)c.phantoms;
             if (c.overflow) { status = ST_CAPACITY; goto finish; }
-            if (c.abort) {  // rows 0 .. cycle - 1 are complete
+            if (c.abort) {  // rows 0 .. cycle - 1 are complete; the counts are those of cycles 1 .. cycle
                 status = ST_TIMEOUT;
                 trace_len = cycle;
                 goto finish;
             }
+            launched += (long long)c.launched;
+            arrivals += (long long)c.n_cand;
+            improved += (long long)c.improved;
+            phantoms += (long long)c.phantoms;
             if (c.n_cand > 0) {  // a real cycle at time Tg
                 if (TRACE && leader) write_row(P, cycle, Time, c.n_active, (long long)c.n_live);
                 updates += (long long)c.n_live;

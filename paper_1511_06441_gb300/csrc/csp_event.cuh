@@ -741,16 +741,16 @@ __device__ void run_event_solve(const Params<W> &P, const EvParams &E, const Gro
                 t_bar += t - t_mark;
                 t_mark = t;
             }
-            launched += (long long)c.launched;
-            arrivals += (long long)c.n_cand;
-            improved += (long long)c.improved;
-            phantoms += (long long)c.phantoms;
             if (c.overflow) { status = ST_CAPACITY; goto finish; }
-            if (c.abort) {  // reported like the sweep form: rows 0 .. cycle - 1
+            if (c.abort) {  // reported like the sweep form: rows 0 .. cycle - 1, counts of cycles 1 .. cycle
                 status = ST_TIMEOUT;
                 trace_len = cycle;
                 goto finish;
             }
+            launched += (long long)c.launched;
+            arrivals += (long long)c.n_cand;
+            improved += (long long)c.improved;
+            phantoms += (long long)c.phantoms;
             updates += live_start;
             cycle++;
             Time = Tn;

@@ -46,12 +46,28 @@ struct ResultSlot {
     long long pad[15];
 };
 
+constexpr int kMaxGroups = 1024;
+
 // Host-mapped control words (written by the host, read by the kernel and vice versa).
 struct HostCtl {
     alignas(128) unsigned long long tail;  // queries written so far
     alignas(128) int shutdown;             // 1 = no more queries: groups exit when idle
     alignas(128) unsigned long long served;
+    // counters written by the kernel (each by one writer at a time)
+    alignas(128) long long wide_queries;   // queries solved by the whole grid
+    long long to_wide, to_narrow;          // switches between the two modes
+    long long narrow_queries[kMaxGroups];  // queries solved by each group
 };
+
+// The server's mode word: generation (high 32 bits), wide flag (bit 31) and the number of
+// narrow groups parked idle (low 31 bits).  Every change is a compare-and-swap.
+constexpr unsigned long long kWideBit = 1ull << 31;
+constexpr long long kCmdExit = -1, kCmdWide = -2, kCmdNarrow = -3;
+
+__device__ __forceinline__ unsigned long long mode_word(unsigned long long gen, bool wide, unsigned long long parked)
+{
+    return (gen << 32) | (wide ? kWideBit : 0ull) | parked;
+}
 
 struct GroupSlot {
     int32_t *label;
@@ -73,33 +89,23 @@ struct ServerArgs {
     const uint32_t *nbw, *nbw_in;  // general graphs: the out- and in-edge tables (null on a lattice)
     long long V;
     int stride[4];
-    const GroupSlot *slots;
-    int group_ctas;
+    const GroupSlot *slots;    // [groups] narrow slots, then the wide slot (whole grid)
+    int group_ctas, groups;
     unsigned long long *head;  // device: next ring position to claim
-    long long *mailbox;        // device: per group, the claimed position (or -1)
-    const HostCtl *hctl;       // host-mapped
+    long long *mailbox;        // device: per group, the claimed position or a command; [groups] = the grid's
+    unsigned long long *mode;  // device: the mode word
+    HostCtl *hctl;             // host-mapped
     const QueryDesc *ring;     // host-mapped
     ResultSlot *results;       // host-mapped
     long long ring_size;
     unsigned long long session_ns;
+    int wide_depth;            // queued queries that end the wide mode; <= 0: no wide mode
 };
 
-template <int D, typename W>
-__global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs S)
+template <typename W>
+__device__ void slot_params(Params<W> &P, const ServerArgs &S, const GroupSlot &slot)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-    init_stage_barriers(sm);
-    uint32_t parity[NSTAGE] = {};
-    const int gid = blockIdx.x / S.group_ctas;
-    const Group g{(uint32_t)(blockIdx.x % S.group_ctas), (uint32_t)S.group_ctas};
-    const GroupSlot &slot = S.slots[gid];
-    // the slot's parameters live in shared memory (read like kernel arguments), not in registers
-    __shared__ Params<W> s_P;
-    if (threadIdx.x == 0) s_P = Params<W>{};
-    __syncthreads();
-    Params<W> &P = s_P;
-    if (threadIdx.x == 0) {
+    P = Params<W>{};
     P.rec = S.rec;
     P.nbw = S.nbw;
     P.nbw_in = S.nbw_in;
@@ -123,38 +129,115 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
     P.touched_n = slot.touched_n;
     P.budget_ns = 120ull * 1000000000ull;
     P.barrier_ns = S.session_ns;  // an idle group waits for work at its barrier
+}
+
+__device__ __forceinline__ unsigned long long ring_tail(const ServerArgs &S)
+{
+    unsigned long long tail;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(tail) : "l"(&S.hctl->tail) : "memory");
+    return tail;
+}
+
+// The grid's leader in the wide mode: the next query to solve with the whole grid, or
+// kCmdNarrow when wide_depth queries or more are waiting (continuous batching then serves
+// them in parallel), or kCmdExit (shutdown with the ring drained, or the session is over).
+__device__ long long wide_claim(const ServerArgs &S, unsigned long long t_begin)
+{
+    for (unsigned int spin = 0;; ++spin) {
+        const unsigned long long tail = ring_tail(S);
+        const unsigned long long h = *(volatile unsigned long long *)S.head;
+        if (h < tail) {
+            if (tail - h >= (unsigned long long)S.wide_depth) {
+                const unsigned long long m = *(volatile unsigned long long *)S.mode;
+                atomicExch(S.mode, mode_word((m >> 32) + 1, false, 0));
+                *(volatile long long *)&S.hctl->to_narrow += 1;
+                return kCmdNarrow;
+            }
+            if (atomicCAS(S.head, h, h + 1) == h) return (long long)h;
+            continue;
+        }
+        if (*(volatile const int *)&S.hctl->shutdown) return kCmdExit;
+        if ((spin & 255u) == 255u && globaltimer_ns() - t_begin > S.session_ns) return kCmdExit;
+        __nanosleep(spin < 64 ? 200 : 2000);
+    }
+}
+
+// A narrow group's leader: the next query for its group, or kCmdWide when the grid has
+// switched to the wide mode, or kCmdExit.  A leader that finds the ring empty parks its
+// group (counted in the mode word); the group that parks last while the ring is empty
+// switches the grid to the wide mode.  A parked leader unparks before it claims.
+__device__ long long narrow_claim(const ServerArgs &S, unsigned long long t_begin)
+{
+    bool parked = false;
+    for (unsigned int spin = 0;; ++spin) {
+        const unsigned long long m = *(volatile unsigned long long *)S.mode;
+        if (m & kWideBit) return kCmdWide;
+        const unsigned long long tail = ring_tail(S);
+        const unsigned long long h = *(volatile unsigned long long *)S.head;
+        if (h < tail) {
+            if (parked) {  // unpark first (fails if the mode word moved on: look again)
+                if (atomicCAS(S.mode, m, m - 1) != m) continue;
+                parked = false;
+            }
+            if (atomicCAS(S.head, h, h + 1) == h) return (long long)h;
+            continue;
+        }
+        if (*(volatile const int *)&S.hctl->shutdown) return kCmdExit;
+        if ((spin & 255u) == 255u && globaltimer_ns() - t_begin > S.session_ns) return kCmdExit;
+        if (!parked && S.wide_depth > 0) {
+            if (atomicCAS(S.mode, m, m + 1) != m) continue;
+            parked = true;
+            if ((m & (kWideBit - 1)) + 1 == (unsigned long long)S.groups) {
+                // every group is idle and the ring is empty: the whole grid takes the next query
+                if (atomicCAS(S.mode, m + 1, mode_word((m >> 32) + 1, true, 0)) == m + 1) {
+                    *(volatile long long *)&S.hctl->to_wide += 1;
+                    return kCmdWide;
+                }
+            }
+            continue;
+        }
+        __nanosleep(spin < 64 ? 200 : 2000);
+    }
+}
+
+template <int D, typename W>
+__global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs S)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    init_stage_barriers(sm);
+    uint32_t parity[NSTAGE] = {};
+    const int gid = blockIdx.x / S.group_ctas;
+    const Group gn{(uint32_t)(blockIdx.x % S.group_ctas), (uint32_t)S.group_ctas};  // this CTA's narrow group
+    const Group gw{blockIdx.x, gridDim.x};                                            // the whole grid
+    // both slots' parameters live in shared memory (read like kernel arguments), not in registers
+    __shared__ Params<W> s_P[2];
+    if (threadIdx.x == 0) {
+        slot_params<W>(s_P[0], S, S.slots[gid]);
+        slot_params<W>(s_P[1], S, S.slots[S.groups]);
     }
     __syncthreads();
-    unsigned long long epoch = 0;
+    unsigned long long epoch[2] = {0, 0};  // barriers passed on the narrow slot and on the wide slot
     const unsigned long long t_begin = globaltimer_ns();
     __shared__ long long s_pos;
     __shared__ QueryDesc s_q;
+    bool wide = S.wide_depth > 0;  // start wide: an idle server answers its first query with every CTA
     for (;;) {
-        if (g.leader()) {
-            // claim the next written query (bounded by the session budget)
-            long long pos = -1;
-            for (unsigned int spin = 0;; ++spin) {
-                unsigned long long tail;
-                asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(tail) : "l"(&S.hctl->tail) : "memory");
-                const unsigned long long h = *(volatile unsigned long long *)S.head;
-                if (h < tail) {
-                    if (atomicCAS(S.head, h, h + 1) == h) {
-                        pos = (long long)h;
-                        break;
-                    }
-                    continue;
-                }
-                if (*(volatile const int *)&S.hctl->shutdown) break;
-                if ((spin & 255u) == 255u && globaltimer_ns() - t_begin > S.session_ns) break;
-                __nanosleep(spin < 64 ? 200 : 2000);
-            }
-            S.mailbox[gid] = pos;
-        }
-        if (!group_sync(P.ctl, epoch, g, P.barrier_ns)) break;
-        if (threadIdx.x == 0) s_pos = *(volatile long long *)&S.mailbox[gid];
+        const Group g = wide ? gw : gn;
+        Params<W> &P = s_P[wide ? 1 : 0];
+        unsigned long long &ep = epoch[wide ? 1 : 0];
+        long long *mail = S.mailbox + (wide ? S.groups : gid);
+        if (g.leader()) *mail = wide ? wide_claim(S, t_begin) : narrow_claim(S, t_begin);
+        if (!group_sync(P.ctl, ep, g, P.barrier_ns)) break;
+        if (threadIdx.x == 0) s_pos = *(volatile long long *)mail;
         __syncthreads();
         const long long pos = s_pos;
-        if (pos < 0) break;
+        __syncthreads();
+        if (pos == kCmdExit) break;
+        if (pos == kCmdWide || pos == kCmdNarrow) {
+            wide = pos == kCmdWide;
+            continue;
+        }
         {
             // the descriptor lives in host memory and ring entries are reused: read it with
             // volatile (uncached) loads into shared memory
@@ -172,16 +255,18 @@ __global__ void __launch_bounds__(TPB, CSP_MIN_CTAS_PER_SM) k_server(ServerArgs 
         const TargetSet T{nullptr, q.nB > 0 ? q.B : nullptr, q.nB, q.nB > 0 ? -1 : q.axis, q.coord};
         // the slot's labels, offers and B bitmap are all zero here (zeroed at creation and
         // undone after every query), so the set-up touches only A and B
-        group_setup_sets<W>(P, g, nullptr, q.A, q.nA, T, epoch, false);
-        run_solve<D, W, false>(P, g, sm, parity, epoch);
-        if (!group_sync(P.ctl, epoch, g, P.barrier_ns)) break;
+        group_setup_sets<W>(P, g, nullptr, q.A, q.nA, T, ep, false);
+        run_solve<D, W, false>(P, g, sm, parity, ep);
+        if (!group_sync(P.ctl, ep, g, P.barrier_ns)) break;
         if (g.leader()) {
             ResultSlot &out = S.results[pos % S.ring_size];
             for (int i = 0; i < R_COUNT; i++) out.r[i] = __ldcg(P.result_dev + i);
             __threadfence_system();
             asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&out.done), "l"(pos + 1) : "memory");
+            if (wide) *(volatile long long *)&S.hctl->wide_queries += 1;
+            else *(volatile long long *)&S.hctl->narrow_queries[gid] += 1;
         }
-        if (!group_undo<W>(P, g, q.A, q.nA, T, epoch)) break;
+        if (!group_undo<W>(P, g, q.A, q.nA, T, ep)) break;
     }
 }
 
@@ -207,8 +292,10 @@ struct csp_server {
     long long ring_size = 0;
     void *ws = nullptr;
     GroupSlot *d_slots = nullptr;
-    unsigned long long *d_head = nullptr;
+    unsigned long long *d_head = nullptr;  // (with the mode word right after it)
     long long *d_mailbox = nullptr;
+    void *wide_ws = nullptr;  // the wide slot's workspace
+    int wide_depth = 0;
     HostCtl *hctl = nullptr;  // pinned, mapped
     QueryDesc *ring = nullptr;
     ResultSlot *results = nullptr;
@@ -291,35 +378,58 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
     const int64_t V = L->V;
     // default: max(2^16, V) flows (at most the lattice's flow bound) plus the chunks a pass
     // may leave part-filled; an explicit capacity is taken as given (rounded up to whole chunks)
-    int64_t pool = opt && opt->pool_capacity > 0
-                       ? opt->pool_capacity
-                       : std::min<int64_t>(std::max<int64_t>(1 << 16, V), (int64_t)std::max(L->flow_bound, 1024ull)) +
-                             chunk_slack(gc);
-    pool = std::min<int64_t>(pool, 0xF0000000ll);
-    pool = (pool + TILE - 1) / TILE * TILE;  // whole chunks
-    const int64_t cand = std::max<int64_t>(V, pool + (int64_t)gc * TILE);  // one region per CTA of a group
-    size_t per = 0;
-    auto take = [&](size_t bytes) {
-        size_t o = per;
-        per = align_up(per + bytes, 256);
-        return o;
+    const int64_t base_pool = opt && opt->pool_capacity > 0
+                                  ? opt->pool_capacity
+                                  : std::min<int64_t>(std::max<int64_t>(1 << 16, V), (int64_t)std::max(L->flow_bound, 1024ull));
+    // one slot's layout for a group of gsize CTAs: returns its bytes and fills the offsets
+    struct Layout {
+        int64_t pool, cand;
+        size_t label, offer, isB, cand_o, ctl, res, touched, tn, pool_o[2][3], fill[2], bytes;
     };
-    const size_t o_label = take(V * 4), o_offer = take(V * 8), o_isB = take(((V + 31) / 32) * 4),
-                 o_cand = take(cand * 4), o_ctl = take(sizeof(Control)), o_res = take(R_COUNT * 8),
-                 o_touched = take(V * 4), o_tn = take(256);
-    size_t o_pool[2][3], o_fill[2];
-    for (int b = 0; b < 2; b++) {
-        for (int f = 0; f < 3; f++) o_pool[b][f] = take((pool + POOL_PAD) * 4);
-        o_fill[b] = take((pool / TILE + 1) * 4);
-    }
+    auto layout = [&](int64_t gsize, bool add_slack) {
+        Layout y{};
+        int64_t pool = add_slack ? base_pool + chunk_slack(gsize) : base_pool;
+        pool = std::min<int64_t>(pool, 0xF0000000ll);
+        pool = (pool + TILE - 1) / TILE * TILE;  // whole chunks
+        y.pool = pool;
+        y.cand = std::max<int64_t>(V, pool + gsize * TILE);  // one region per CTA of the group
+        size_t per = 0;
+        auto take = [&](size_t bytes) {
+            size_t o = per;
+            per = align_up(per + bytes, 256);
+            return o;
+        };
+        y.label = take(V * 4);
+        y.offer = take(V * 8);
+        y.isB = take(((V + 31) / 32) * 4);
+        y.cand_o = take(y.cand * 4);
+        y.ctl = take(sizeof(Control));
+        y.res = take(R_COUNT * 8);
+        y.touched = take(V * 4);
+        y.tn = take(256);
+        for (int b = 0; b < 2; b++) {
+            for (int f = 0; f < 3; f++) y.pool_o[b][f] = take((pool + POOL_PAD) * 4);
+            y.fill[b] = take((pool / TILE + 1) * 4);
+        }
+        y.bytes = per;
+        return y;
+    };
+    const bool explicit_pool = opt && opt->pool_capacity > 0;
+    const Layout ln = layout(gc, !explicit_pool);
+    const size_t per = ln.bytes;
     if (opt && opt->memory_budget > 0) groups = (int)std::max<int64_t>(1, std::min<int64_t>(groups, opt->memory_budget / per));
+    groups = std::min(groups, kMaxGroups);
+    const int wide_depth = opt && opt->wide_depth != 0 ? opt->wide_depth : 2;
+    const Layout lw = layout((int64_t)groups * gc, true);
     s->groups = groups;
     s->group_ctas = gc;
+    s->wide_depth = wide_depth;
     s->ring_size = opt && opt->queue_capacity > 0 ? opt->queue_capacity : 4 * groups;
     e = cudaMalloc(&s->ws, per * groups);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_slots, groups * sizeof(GroupSlot));
+    if (e == cudaSuccess && wide_depth > 0) e = cudaMalloc(&s->wide_ws, lw.bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_slots, (groups + 1) * sizeof(GroupSlot));
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_head, 256);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_mailbox, groups * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_mailbox, (groups + 1) * sizeof(long long));
     const size_t host_bytes = sizeof(HostCtl) + s->ring_size * (sizeof(QueryDesc) + sizeof(ResultSlot)) + 256;
     if (e == cudaSuccess) e = cudaHostAlloc(&s->host_block, host_bytes, cudaHostAllocMapped);
     if (e != cudaSuccess) {
@@ -331,31 +441,38 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
     s->hctl = (HostCtl *)s->host_block;
     s->ring = (QueryDesc *)((char *)s->host_block + sizeof(HostCtl));
     s->results = (ResultSlot *)((char *)s->ring + s->ring_size * sizeof(QueryDesc));
-    std::vector<GroupSlot> slots(groups);
-    char *ws = (char *)s->ws;
-    for (int i = 0; i < groups; i++) {
-        char *b = ws + per * i;
-        GroupSlot &g = slots[i];
-        g.label = (int32_t *)(b + o_label);
-        g.offer = (unsigned long long *)(b + o_offer);
-        g.isB = (uint32_t *)(b + o_isB);
-        g.cand = (uint32_t *)(b + o_cand);
-        g.cand_cap = (unsigned int)cand;
-        g.pool_cap = (unsigned int)pool;
+    auto carve = [&](char *b, const Layout &y) {
+        GroupSlot g{};
+        g.label = (int32_t *)(b + y.label);
+        g.offer = (unsigned long long *)(b + y.offer);
+        g.isB = (uint32_t *)(b + y.isB);
+        g.cand = (uint32_t *)(b + y.cand_o);
+        g.cand_cap = (unsigned int)y.cand;
+        g.pool_cap = (unsigned int)y.pool;
         for (int q = 0; q < 2; q++) {
-            g.ed[q] = (uint32_t *)(b + o_pool[q][0]);
-            g.qa[q] = (int32_t *)(b + o_pool[q][1]);
-            g.ta[q] = (int32_t *)(b + o_pool[q][2]);
-            g.fill[q] = (uint32_t *)(b + o_fill[q]);
+            g.ed[q] = (uint32_t *)(b + y.pool_o[q][0]);
+            g.qa[q] = (int32_t *)(b + y.pool_o[q][1]);
+            g.ta[q] = (int32_t *)(b + y.pool_o[q][2]);
+            g.fill[q] = (uint32_t *)(b + y.fill[q]);
         }
-        g.ctl = (Control *)(b + o_ctl);
-        g.result = (long long *)(b + o_res);
-        g.touched = (uint32_t *)(b + o_touched);
-        g.touched_n = (unsigned int *)(b + o_tn);
-    }
+        g.ctl = (Control *)(b + y.ctl);
+        g.result = (long long *)(b + y.res);
+        g.touched = (uint32_t *)(b + y.touched);
+        g.touched_n = (unsigned int *)(b + y.tn);
+        return g;
+    };
+    std::vector<GroupSlot> slots(groups + 1);
+    char *ws = (char *)s->ws;
+    for (int i = 0; i < groups; i++) slots[i] = carve(ws + per * i, ln);
+    // the wide slot (the whole grid); with no wide mode it repeats slot 0 and is never used
+    slots[groups] = wide_depth > 0 ? carve((char *)s->wide_ws, lw) : slots[0];
     if (e == cudaSuccess) e = cudaMemset(ws, 0, per * groups);  // all labels, offers, bitmaps and controls
-    if (e == cudaSuccess) e = cudaMemcpy(s->d_slots, slots.data(), groups * sizeof(GroupSlot), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && wide_depth > 0) e = cudaMemset(s->wide_ws, 0, lw.bytes);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->d_slots, slots.data(), (groups + 1) * sizeof(GroupSlot), cudaMemcpyHostToDevice);
+    const unsigned long long mode0 = wide_depth > 0 ? (1ull << 31) : 0ull;  // start wide
     if (e == cudaSuccess) e = cudaMemset(s->d_head, 0, 256);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_head + 1, &mode0, 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     ServerArgs a{};
     if (e == cudaSuccess) {
@@ -366,11 +483,14 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
         for (int k = 0; k < 4; k++) a.stride[k] = L->stride[k];
         a.slots = s->d_slots;
         a.group_ctas = gc;
+        a.groups = groups;
         a.head = s->d_head;
+        a.mode = s->d_head + 1;
         a.mailbox = s->d_mailbox;
+        a.wide_depth = wide_depth;
         void *p = nullptr;
         e = cudaHostGetDevicePointer(&p, s->host_block, 0);
-        a.hctl = (const HostCtl *)p;
+        a.hctl = (HostCtl *)p;
         a.ring = (const QueryDesc *)((char *)p + sizeof(HostCtl));
         a.results = (ResultSlot *)((char *)a.ring + s->ring_size * sizeof(QueryDesc));
         a.ring_size = s->ring_size;
@@ -398,6 +518,22 @@ csp_status csp_server_info(const csp_server *s, int32_t *groups, int32_t *group_
     if (groups) *groups = s->groups;
     if (group_ctas) *group_ctas = s->group_ctas;
     if (queue_capacity) *queue_capacity = s->ring_size;
+    return CSP_OK;
+}
+
+csp_status csp_server_stats(const csp_server *s, int64_t *wide_queries, int64_t *narrow_queries, int64_t *to_wide,
+                            int64_t *to_narrow)
+{
+    if (!s || !s->hctl) return CSP_ERR_INVALID;
+    const volatile HostCtl *h = s->hctl;
+    if (wide_queries) *wide_queries = h->wide_queries;
+    if (narrow_queries) {
+        long long n = 0;
+        for (int i = 0; i < s->groups; i++) n += h->narrow_queries[i];
+        *narrow_queries = n;
+    }
+    if (to_wide) *to_wide = h->to_wide;
+    if (to_narrow) *to_narrow = h->to_narrow;
     return CSP_OK;
 }
 
@@ -501,6 +637,7 @@ csp_status csp_server_destroy(csp_server *s)
     if (s->d_head) cudaFree(s->d_head);
     if (s->d_slots) cudaFree(s->d_slots);
     if (s->ws) cudaFree(s->ws);
+    if (s->wide_ws) cudaFree(s->wide_ws);
     delete s;
     return st;
 }

@@ -46,3 +46,32 @@ def test_cpu_baseline_batched_on_tiny_instances():
     out = bench.cpu_baseline_batched(insts, ups, budget_updates=sum(ups), cap_updates=max(ups), cores=2)
     assert out["kind"] == "oracle" and out["cores"] == 2 and out["value"] > 0
     assert out["whole_batch_instances_per_s_estimate"] > 0 and "12 of 12" in out["sample"]
+
+
+def test_algorithmic_bytes_and_roofline_block():
+    sys.path.insert(0, ROOT)
+    import bench
+    # 8 B per update, 13 per arrival, 6 per edge slot of an improved vertex, 12 per started flow
+    assert bench.alg_bytes(6, 10, 2, 3, 4) == 80 + 26 + 108 + 48
+    rec = [0] * 16
+    rec[7], rec[13], rec[14], rec[8] = 10, 2, 3, 4
+    assert bench.alg_bytes_of(6, rec) == 262
+    r = bench.roofline_block(2e9, 0.5, "k", traffic=3e9)
+    assert r["bound"] == "hbm" and abs(r["achieved"] - 4.0) < 1e-12 and r["frac"] == r["achieved"] / r["peak"]
+    assert abs(r["dram_gbs"] - 6.0) < 1e-12 and r["unit"] == "GB/s"
+
+
+def test_summary_repeats_the_section_headlines():
+    sys.path.insert(0, ROOT)
+    import bench
+    line = {"value": 5.0, "roofline": {"frac": 0.1}, "e2e": {"value": 4.0},
+            "engines": {"event_vs_sweep": 0.3},
+            "batched": {"instances_per_s": 30.0, "plain_instances_per_s": 15.0, "speedup_vs_plain": 2.0,
+                        "agree_with_plain": 512, "roofline": {"frac": 0.2}},
+            "serving": {"queries": 10, "rates": [
+                {"rate_x_saturation": 0.5, "served": {"p99_ms": 3.0, "equal_to_alone": 10}, "plain": {"p99_ms": 4.0}},
+                {"rate_x_saturation": 1.0, "served": {"p99_ms": 5.0, "equal_to_alone": 9}, "plain": {"p99_ms": 4.0}}]}}
+    s = bench.summary(line)
+    assert s["updates_per_s"] == 5.0 and s["batched"]["speedup_vs_plain"] == 2.0
+    assert s["serving"]["served_p99_le_plain_everywhere"] is False and s["serving"]["equal_to_alone"] == 9
+    assert s["event_form_vs_sweep"] == 0.3

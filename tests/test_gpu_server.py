@@ -81,3 +81,23 @@ def test_plain_replay_and_bad_queries(csp, setup):
     with pytest.raises(csp.CspError):
         srv.submit(bad)
     srv.close()
+
+
+@pytest.mark.parametrize("wide_depth", [2, 4, -1])
+def test_wide_and_narrow_modes_give_the_alone_results(csp, setup, wide_depth):
+    # a burst (the backlog switches the whole-grid mode to groups), then queries one at a time
+    # with gaps (every group idle again: back to the whole grid), then another burst
+    ext, f1, f2, lat, qs, alone = setup
+    srv = csp.Server(lat, group_ctas=2, max_groups=4, queue_capacity=64, session_seconds=120, wide_depth=wide_depth)
+    n = len(qs)
+    arrivals = np.concatenate([np.zeros(n), 0.05 + 0.01 * np.arange(n), np.full(n, 0.05 + 0.01 * n + 0.05)])
+    got, lat_s, mk = srv.replay(qs * 3, arrivals)
+    assert [_key(r) for r in got] == [_key(r) for r in alone] * 3
+    assert all(r.status == csp.OK for r in got)
+    st = srv.stats()
+    srv.close()
+    assert st["wide_queries"] + st["narrow_queries"] == 3 * n
+    if wide_depth > 0:
+        assert st["wide_queries"] > 0 and st["narrow_queries"] > 0 and st["to_narrow"] >= 1 and st["to_wide"] >= 1
+    else:
+        assert st["wide_queries"] == 0 and st["to_wide"] == 0 and st["to_narrow"] == 0

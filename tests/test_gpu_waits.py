@@ -101,13 +101,15 @@ def test_idle_server_session_runs_out(csp, small):
     inst, want = small
     lat = csp.Lattice(inst.extents, inst.f1, inst.f2)
     srv = csp.Server(lat, group_ctas=4, max_groups=2, session_seconds=1.0)
-    t = srv.submit(type("Q", (), {"A": inst.A, "B": inst.B, "M": 300, "axis": -1, "coord": 0})(),
+    B = inst.B[:40]  # (a server query carries at most 64 explicit targets)
+    ref = lat.solve(inst.A[:64], B, 300)
+    t = srv.submit(type("Q", (), {"A": inst.A[:64], "B": B, "M": 300, "axis": -1, "coord": 0})(),
                    use_hyperplane=False)
     t0 = time.perf_counter()
     r = None
     while r is None and time.perf_counter() - t0 < 10:
         r = srv.poll(t)
-    assert r is not None and r.status == csp.OK and r.answer() == want.answer()
+    assert r is not None and r.status == csp.OK and r.answer() == ref.answer()
     time.sleep(2.0)  # idle past the session: the persistent kernel gives up waiting and ends
     t0 = time.perf_counter()
     srv.close()
@@ -121,10 +123,11 @@ def test_full_query_ring_refuses(csp, small):
     ext = [512, 512]
     f1, f2 = synth.uniform_weights(ext, 1, 16, 5)
     lat = csp.Lattice(ext, f1, f2)
-    srv = csp.Server(lat, group_ctas=1, max_groups=1, queue_capacity=2, session_seconds=60.0)
+    srv = csp.Server(lat, group_ctas=1, max_groups=1, queue_capacity=2, session_seconds=60.0,
+                     pool_capacity=1 << 22)
     Q = type("Q", (), {})
     long_q = Q()
-    long_q.A, long_q.B, long_q.M, long_q.axis, long_q.coord = synth.face(ext, 0, 0)[:64], None, 50_000, 0, 511
+    long_q.A, long_q.B, long_q.M, long_q.axis, long_q.coord = synth.face(ext, 0, 0)[:64], None, 6000, 0, 511
     tickets = [srv.submit(long_q), srv.submit(long_q)]  # one CTA: these take a while each
     with pytest.raises(csp.CspError) as e:
         srv.submit(long_q)

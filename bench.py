@@ -91,7 +91,7 @@ def traffic_record(name: str):
     try:
         with open(path) as f:
             pj = json.load(f)
-        if pj.get("kernel_source_sha256") == _kernel_sha():
+        if pj.get("kernel_source_sha256") == _kernel_sha(TRAFFIC[name]["files"]):
             return pj
     except Exception:
         pass
@@ -309,18 +309,12 @@ def run_ours(args):
     achieved /= 1e9
     peak, peak_src = peaks()
     traffic, dram = None, None
-    prof = os.path.join(ROOT, "profiles", "k_cycle_cube128_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                pj = json.load(f)
-            if pj.get("kernel_source_sha256") == _kernel_sha():
-                per_m = pj.get("traffic_bytes_per_launch", {})
-                traffic = float(np.mean([per_m[str(M)] for M in M_SWEEP]))
-                dram = dram_rate([per_m[str(M)] for M in M_SWEEP],
-                                 [float(np.mean([kern_ms[k][i] for k in range(K)])) for i in range(nM)])
-        except Exception:
-            traffic, dram = None, None
+    pj = traffic_record("k_cycle_cube128_traffic.json")
+    if pj is not None:
+        per_m = pj["traffic_bytes_per_launch"]
+        traffic = float(np.mean([per_m[str(M)] for M in M_SWEEP]))
+        dram = dram_rate([per_m[str(M)] for M in M_SWEEP],
+                         [float(np.mean([kern_ms[k][i] for k in range(K)])) for i in range(nM)])
 
     # end to end through the synchronous C-ABI call with host buffers
     e2e = None
@@ -388,7 +382,8 @@ def run_ours(args):
     if world == 1 and args.batch:
         line["batched"] = bench_batched(csp, synth)
     if world == 1 and args.serve > 0:
-        line["serving"] = bench_serving(csp, synth, args.serve, args.no_cpu_baseline)
+        line["serving"] = bench_serving(csp, synth, args.serve, args.no_cpu_baseline,
+                                        [float(x) for x in args.serve_rates.split(",")], bool(args.serve_plain))
     if world == 1 and args.anticorrelated:
         line["anticorrelated"] = bench_anticorrelated(csp, synth, args.no_cpu_baseline)
     if world == 1 and args.open_problems:
@@ -450,7 +445,13 @@ def bench_engines(csp, lat, A, B, stream, trace, trace_cap, rec, sweep_out, swee
     same = bool((got[:, 1:9] == sweep_out[:, 1:9]).all())
     sweep_avg = [float(np.mean([sweep_ms[k][i] for k in range(K)])) for i in range(len(M_SWEEP))]
     upd = int(got[:, 7].sum())
-    return {"event_kernel_ms": ms, "sweep_kernel_ms": sweep_avg, "same_results": same,
+    tr = traffic_record("k_event_cube128_traffic.json")
+    ev_traffic = None
+    if tr is not None:
+        per_m = tr["traffic_bytes_per_launch"]
+        ev_traffic = {"bytes_per_launch": [per_m[str(M)] for M in M_SWEEP],
+                      "dram_gbs": dram_rate([per_m[str(M)] for M in M_SWEEP], ms)}
+    return {"event_kernel_ms": ms, "sweep_kernel_ms": sweep_avg, "same_results": same, "event_dram": ev_traffic,
             "event_updates_per_s": upd / (sum(ms) / 1e3), "event_vs_sweep": sum(sweep_avg) / sum(ms),
             "default_form": lat.default_engine(),
             "note": "event form: per-edge queues and a calendar of arrival times (CSP_OPT_EVENT); the default "
@@ -731,7 +732,7 @@ def cpu_baseline_batched(insts, updates, budget_updates=8e9, cap_updates=6e8, co
             "whole_batch_instances_per_s_estimate": len(insts) / est}
 
 
-def bench_serving(csp, synth, n_queries, no_cpu=False):
+def bench_serving(csp, synth, n_queries, no_cpu=False, rates=None, plain=True):
     """48^4 lattice, query stream served with continuous batching vs answered one at a time."""
     import torch
     ext, f1, f2 = synth.serving_lattice(48, 4, 5)
@@ -746,30 +747,36 @@ def bench_serving(csp, synth, n_queries, no_cpu=False):
     mu = 1.0 / float(np.mean(t_svc))
     key = lambda r: (r.answer(), r.cycles, r.updates)  # noqa: E731
     max_pool = max(r.max_pool for r in alone)
-    rates = (0.25, 0.5, 0.75, 1.0, 1.25)
+    rates = tuple(rates or (0.25, 0.5, 0.75, 1.0, 1.25))
     out = {"workload": f"lattice4d_48_U1-20_{n_queries}queries_1-64src_hyperplaneB_M200-2000",
            "queries": n_queries, "plain_saturation_qps": mu, "service_ms_p50": 1e3 * float(np.median(t_svc)),
            "rates": []}
-    srv = csp.Server(lat, group_ctas=32, pool_capacity=max(1 << 16, int(1.25 * max_pool)), session_seconds=600)
+    srv = csp.Server(lat, group_ctas=16, wide_depth=3, pool_capacity=max(1 << 16, int(1.25 * max_pool)),
+                     session_seconds=900)
     out["slots"] = srv.groups
     out["ctas_per_slot"] = srv.group_ctas
+    out["modes"] = "the whole grid answers one query at a time while fewer than 3 wait; 16-CTA groups serve a " \
+                   "backlog in parallel until all are idle (csp_server_options.wide_depth)"
     served = {}
     for m in rates:
         arr = synth.poisson_arrivals(n_queries, m * mu, seed=5)
+        s0 = srv.stats()
         got, L, mk = srv.replay(qs, arr)
-        served[m] = (got, L, mk)
+        s1 = srv.stats()
+        served[m] = (got, L, mk, {k: s1[k] - s0[k] for k in s1})
     srv.close()
     alg = sum(alg_bytes(8, x.updates, x.arrivals, x.improved, x.launched) for x in alone)
     tr = traffic_record("k_server_lattice4d48_traffic.json")
     for m in rates:
-        got, L, mk = served[m]
+        got, L, mk, modes = served[m]
         arr = synth.poisson_arrivals(n_queries, m * mu, seed=5)
-        pg, PL, pmk = csp.plain_replay(lat, qs, arr)
+        pg, PL, pmk = csp.plain_replay(lat, qs, arr) if plain else (None, np.full(1, np.nan), np.nan)
         out["rates"].append({
             "rate_x_saturation": m, "rate_qps": m * mu,
             "served": {"qps": n_queries / mk, "p50_ms": 1e3 * float(np.median(L)),
                        "p99_ms": 1e3 * float(np.quantile(L, 0.99)),
                        "equal_to_alone": sum(key(a) == key(b) for a, b in zip(got, alone)),
+                       "answered_by": modes,
                        "roofline": roofline_block(alg, mk, "k_server (persistent, the whole stream)",
                                                   note="algorithmic bytes of all queries over the stream's makespan "
                                                        "(arrival-limited below saturation)")},
@@ -839,13 +846,62 @@ def dram_rate(traffic_bytes, kernel_ms):
     return float(np.mean([b / (ms / 1e3) for b, ms in zip(traffic_bytes, kernel_ms)])) / 1e9
 
 
-def _kernel_sha():
+# Per-launch DRAM traffic records under profiles/: the sources each kernel is built from (a record
+# counts only while they are unchanged), the launch labels, and which captured launches they take.
+TRAFFIC = {
+    "k_cycle_cube128_traffic.json": {"files": ("csp_device.cuh", "csp_solver.cu"), "labels": ["400", "800", "1600"],
+                                     "take": [0, 1, 2], "kernel": "k_cycle<3, uint8, trace=1> (128^3 cube)"},
+    "k_event_cube128_traffic.json": {"files": ("csp_device.cuh", "csp_event.cuh", "csp_event.cu"),
+                                     "labels": ["400", "800", "1600"], "take": [1, 3, 5],
+                                     "kernel": "k_event<3, uint8, trace=1> (128^3 cube, second of two launches per M)"},
+    "k_batch_batch512_traffic.json": {"files": ("csp_device.cuh", "csp_batch.cu"), "labels": None, "take": [0],
+                                      "kernel": "k_batch<uint8> (512 mixed instances, tuned schedule)"},
+    "k_server_lattice4d48_traffic.json": {"files": ("csp_device.cuh", "csp_server.cu"), "labels": None, "take": [0],
+                                          "kernel": "k_server<4, uint8> (48^4 lattice, the whole session)"},
+    "k_cycle_anticorr4096_traffic.json": {"files": ("csp_device.cuh", "csp_solver.cu"), "labels": None, "take": [0],
+                                          "kernel": "k_cycle<2, uint16, trace=0> (4096^2 anti-correlated, the whole solve)"},
+}
+
+
+def _kernel_sha(files=("csp_device.cuh", "csp_solver.cu")):
     import hashlib
     h = hashlib.sha256()
-    for f in ("csp_device.cuh", "csp_solver.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1511_06441_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def record_traffic(csv_path: str, name: str, command: str, out_dir: str = "") -> dict:
+    """Writes profiles/<name> from an ncu CSV (--metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    gpu__time_duration.sum --csv --print-units base): per captured launch, DRAM read + write bytes."""
+    import csv
+    spec = TRAFFIC[name]
+    launches = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f) if len(r) > 5]
+    head = rows[0]
+    col = {k: head.index(k) for k in ("ID", "Metric Name", "Metric Value")}
+    for r in rows[1:]:
+        if not r[col["ID"]].isdigit():
+            continue
+        d = launches.setdefault(int(r[col["ID"]]), {})
+        d[r[col["Metric Name"]]] = float(r[col["Metric Value"]].replace(",", ""))
+    ids = sorted(launches)
+    picked = [launches[ids[i]] for i in spec["take"]]
+    traffic = [x["dram__bytes_read.sum"] + x["dram__bytes_write.sum"] for x in picked]
+    dur = [x["gpu__time_duration.sum"] for x in picked]
+    rec = {"kernel": spec["kernel"], "command": command, "kernel_sources": list(spec["files"]),
+           "kernel_source_sha256": _kernel_sha(spec["files"])}
+    if spec["labels"]:
+        rec["traffic_bytes_per_launch"] = dict(zip(spec["labels"], traffic))
+        rec["duration_ns_under_ncu"] = dict(zip(spec["labels"], dur))
+    else:
+        rec["traffic_bytes_per_launch"] = traffic[0]
+        rec["duration_ns_under_ncu"] = dur[0]
+    with open(os.path.join(out_dir or os.path.join(ROOT, "profiles"), name), "w") as f:
+        json.dump(rec, f, indent=1)
+    return rec
 
 
 def main():
@@ -869,9 +925,18 @@ def main():
                     help="also count the active vertices at time t = 4096 on the environments omega_j (N=1)")
     ap.add_argument("--anticorrelated", type=int, default=1,
                     help="also time the 4096^2 anti-correlated solve and its path (N=1; ~1.5 min)")
+    ap.add_argument("--serve-rates", default="0.25,0.5,0.75,1.0,1.25",
+                    help="serving rates as multiples of the plain solver's saturation rate")
+    ap.add_argument("--serve-plain", type=int, default=1, help="also replay the stream one query at a time")
     ap.add_argument("--serve", type=int, default=10000,
                     help="queries per rate for the serving comparison on the 48^4 lattice (0 = skip; N=1 only)")
+    ap.add_argument("--record-traffic", nargs=3, metavar=("NCU_CSV", "NAME", "COMMAND"),
+                    help="write profiles/NAME (a per-launch DRAM traffic record) from an ncu CSV and exit")
     args = ap.parse_args()
+    if args.record_traffic:
+        csv_path, name, command = args.record_traffic
+        print(json.dumps(record_traffic(csv_path, name, command)))
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

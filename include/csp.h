@@ -350,7 +350,7 @@ csp_status csp_reconstruct_fast(csp_lattice *lat, const int64_t *A, int64_t nA, 
 typedef struct csp_server csp_server;
 
 typedef struct {
-    int32_t group_ctas;       /* CTAs per query slot; 0 = 8 */
+    int32_t group_ctas;       /* CTAs per query slot; 0 = 16 */
     int32_t max_groups;       /* query slots; 0 = as many as fit on the GPU */
     int64_t pool_capacity;    /* flow slots per pool buffer per slot (whole chunks of 2048, up to two
                                  part-filled per CTA); 0 = max(2^16, V) capped by the flow bound, plus
@@ -359,7 +359,7 @@ typedef struct {
     int64_t memory_budget;    /* bytes for all slots together; 0 = no limit beyond max_groups */
     int64_t queue_capacity;   /* ring entries (queries submitted and not yet collected); 0 = 4 x slots */
     double session_seconds;   /* the persistent kernel gives up waiting after this long; 0 = 600 */
-    int32_t wide_depth;       /* two modes (0 = 2): while fewer than wide_depth queries wait, the whole grid
+    int32_t wide_depth;       /* two modes (0 = 3): while fewer than wide_depth queries wait, the whole grid
                                  answers one query at a time (the latency of a plain solve without its
                                  launch); from wide_depth waiting queries on, the groups serve them in
                                  parallel (continuous batching) until every group is idle again.  -1 = groups

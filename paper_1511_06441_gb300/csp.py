@@ -580,7 +580,7 @@ class Server:
     def __init__(self, lattice: "Lattice", *, group_ctas: int = 0, max_groups: int = 0, pool_capacity: int = 0,
                  memory_budget: int = 0, queue_capacity: int = 0, session_seconds: float = 0.0, wide_depth: int = 0):
         """``wide_depth``: waiting queries that switch the whole-grid (wide) mode to groups;
-        0 = the library default (2), -1 = groups only."""
+        0 = the library default (3), -1 = groups only."""
         L = _server_api()
         opt = CspServerOptions(group_ctas, max_groups, pool_capacity, memory_budget, queue_capacity, session_seconds,
                                int(wide_depth), 0)

@@ -371,7 +371,7 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
         return e != cudaSuccess ? cuda_fail(e, "server kernel attributes") : CSP_ERR_CUDA;
     }
     const int max_ctas = per_sm * num_sms(L->device);
-    int gc = opt && opt->group_ctas > 0 ? opt->group_ctas : 8;
+    int gc = opt && opt->group_ctas > 0 ? opt->group_ctas : 16;
     gc = std::max(1, std::min(gc, max_ctas));
     int groups = max_ctas / gc;
     if (opt && opt->max_groups > 0) groups = std::min(groups, opt->max_groups);
@@ -419,7 +419,7 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
     const size_t per = ln.bytes;
     if (opt && opt->memory_budget > 0) groups = (int)std::max<int64_t>(1, std::min<int64_t>(groups, opt->memory_budget / per));
     groups = std::min(groups, kMaxGroups);
-    const int wide_depth = opt && opt->wide_depth != 0 ? opt->wide_depth : 2;
+    const int wide_depth = opt && opt->wide_depth != 0 ? opt->wide_depth : 3;
     const Layout lw = layout((int64_t)groups * gc, true);
     s->groups = groups;
     s->group_ctas = gc;

@@ -75,3 +75,21 @@ def test_summary_repeats_the_section_headlines():
     assert s["updates_per_s"] == 5.0 and s["batched"]["speedup_vs_plain"] == 2.0
     assert s["serving"]["served_p99_le_plain_everywhere"] is False and s["serving"]["equal_to_alone"] == 9
     assert s["event_form_vs_sweep"] == 0.3
+
+
+def test_traffic_record_from_an_ncu_csv(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    head = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",' \
+           '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = []
+    for i, (rd, wr, t) in enumerate([(1, 2, 10), (10, 20, 100), (3, 4, 30), (30, 40, 300), (5, 6, 50), (50, 60, 500)]):
+        for m, v in (("dram__bytes_read.sum", rd), ("dram__bytes_write.sum", wr), ("gpu__time_duration.sum", t)):
+            rows.append(f'"{i}","1","python","h","k_event","1","7","(512, 1, 1)","(304, 1, 1)","0","10.3",'
+                        f'"Command line profiler metrics","{m}","byte","{v:,}"\n')
+    csv = tmp_path / "t.csv"
+    csv.write_text("==PROF== noise\n" + head + "".join(rows))
+    rec = bench.record_traffic(str(csv), "k_event_cube128_traffic.json", "cmd", out_dir=str(tmp_path))
+    assert rec["traffic_bytes_per_launch"] == {"400": 30.0, "800": 70.0, "1600": 110.0}  # launches 1, 3, 5
+    assert rec["duration_ns_under_ncu"]["1600"] == 500.0
+    assert rec["kernel_source_sha256"] == bench._kernel_sha(bench.TRAFFIC["k_event_cube128_traffic.json"]["files"])

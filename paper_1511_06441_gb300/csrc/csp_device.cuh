@@ -37,13 +37,16 @@ namespace csp {
 #ifndef CSP_MIN_CTAS_PER_SM
 #define CSP_MIN_CTAS_PER_SM 2
 #endif
+#ifndef CSP_NSTAGE
+#define CSP_NSTAGE 3
+#endif
 constexpr int TPB = CSP_TPB;        // threads per CTA
 constexpr int IPT = CSP_IPT;        // items per thread per tile
 constexpr int TILE = TPB * IPT;     // items per tile
 constexpr int NWARP = TPB / 32;
 constexpr int TIME_LIMIT = 1 << 30; // arrival times must stay below this
 constexpr int POOL_PAD = 64;        // extra elements after each pool array (bulk copies round up)
-constexpr int NSTAGE = 3;           // input stages of the sweep (tiles in flight per CTA)
+constexpr int NSTAGE = CSP_NSTAGE;  // input stages of the sweep (tiles in flight per CTA)
 constexpr int GRAPH = 5;            // template value of D for a general graph (Section 1): up to 8 slots
 
 // Directions (edge slots) per vertex: 2d on a lattice of dimension d, 8 on a general graph.

@@ -376,6 +376,7 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
         "engines": engines,
+        "shape": shape_info(csp),
     }
     del lat, f1, f2, flush, trace, rec
     torch.cuda.empty_cache()
@@ -396,6 +397,20 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(inst, ORACLE_SAMPLE_CYCLES)
     line["summary"] = summary(line)  # last, so that a tail of the line keeps it
     print(json.dumps(line), flush=True)
+
+
+def shape_info(csp) -> dict:
+    """The block shape the library was built with and, if the shape tuner cached its choice, what it
+    measured (paper_1511_06441_gb300/shape.json)."""
+    out = {"built": csp.build_shape()}
+    path = os.path.join(ROOT, "paper_1511_06441_gb300", "shape.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            t = json.load(f)
+        out["tuner"] = {"chosen": t.get("chosen_label"), "gain_over_default": t.get("gain_over_default"),
+                        "measured": [[m["shape"], m.get("cube128_step_ms"), m.get("batch128_ms")]
+                                     for m in t.get("measured", [])]}
+    return out
 
 
 def summary(line: dict) -> dict:

@@ -113,6 +113,13 @@ typedef struct {
  * and the solve returns CSP_ERR_BARRIER with the device left usable.  Needs two CTAs or more. */
 #define CSP_OPT_TEST_ABSENT_CTA 8
 
+/* The block shape this library was built with (build parameters chosen by the shape tuner,
+ * paper_1511_06441_gb300/tune.py, and cached in paper_1511_06441_gb300/shape.json):
+ * shape[0] threads per CTA, shape[1] flows per thread per tile (the flow-pool chunk is their
+ * product), shape[2] tiles in flight per CTA in the sweep, shape[3] CTAs per SM of the solve and
+ * server kernels, shape[4] CTAs per SM of the batch kernel.  The paper has no counterpart. */
+void csp_build_shape(int32_t *shape);
+
 /* Text for a status code (static storage). */
 const char *csp_status_string(csp_status s);
 

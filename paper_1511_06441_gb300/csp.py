@@ -85,6 +85,8 @@ def lib():
         L.csp_reconstruct_fast.argtypes = [vp, i64p, i64, i64p, i64, i64, ctypes.POINTER(CspOptions), i64,
                                            ctypes.POINTER(CspResult), i64p, i64, i64p]
         L.csp_reconstruct_path.restype = ctypes.c_int
+        L.csp_build_shape.argtypes = [ctypes.POINTER(ctypes.c_int32)]
+        L.csp_build_shape.restype = None
         L.csp_default_engine.argtypes = [vp]
         L.csp_default_engine.restype = ctypes.c_int32
         L.csp_event_phase_times.argtypes = [vp, i64p]
@@ -96,6 +98,13 @@ def lib():
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def build_shape() -> dict:
+    """``csp_build_shape``: the block shape the loaded library was built with."""
+    out = (ctypes.c_int32 * 5)()
+    lib().csp_build_shape(out)
+    return dict(zip(("tpb", "ipt", "nstage", "min_ctas_per_sm", "batch_min_ctas_per_sm"), [int(x) for x in out]))
 
 
 def _check(status: int, where: str):

@@ -1,0 +1,162 @@
+"""Block-shape tuner for the cycle kernels: builds the library with each candidate shape
+(threads per CTA, flows per thread per tile, tiles in flight, CTAs per SM of the solve and
+batch kernels), times every build on the tuning workloads in a process of its own, checks
+that each gives exactly the default build's results, and caches the fastest shape in
+shape.json, which build() compiles with from then on.
+
+    python -m paper_1511_06441_gb300.tune            # measure and print (needs a GPU)
+    python -m paper_1511_06441_gb300.tune --write    # and cache the choice
+
+Tuning workloads: the 128^3 cube solved for M = 400, 800 and 1600 with a trace (the
+benchmark's step; kernel time by CUDA events, best of three) and every fourth instance of
+the 512 mixed batch instances in one tuned batched launch.  The score of a shape is the
+sum over workloads of its time over the default shape's time.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+
+DEFAULT = {"tpb": 512, "ipt": 4, "nstage": 3, "min_ctas_per_sm": 2, "batch_min_ctas_per_sm": 1}
+CANDIDATES = [
+    DEFAULT,
+    {"tpb": 512, "ipt": 4, "nstage": 4, "min_ctas_per_sm": 2, "batch_min_ctas_per_sm": 1},
+    {"tpb": 512, "ipt": 4, "nstage": 3, "min_ctas_per_sm": 2, "batch_min_ctas_per_sm": 2},
+    {"tpb": 384, "ipt": 4, "nstage": 3, "min_ctas_per_sm": 3, "batch_min_ctas_per_sm": 1},
+    {"tpb": 256, "ipt": 4, "nstage": 3, "min_ctas_per_sm": 4, "batch_min_ctas_per_sm": 2},
+    {"tpb": 256, "ipt": 8, "nstage": 3, "min_ctas_per_sm": 4, "batch_min_ctas_per_sm": 2},
+]
+
+
+def label(shape: dict) -> str:
+    return "{tpb}x{ipt}x{nstage}/{min_ctas_per_sm}/{batch_min_ctas_per_sm}".format(**shape)
+
+
+def measure(lib_path: str) -> dict:
+    """Times the tuning workloads with the library at lib_path (run in a fresh process: one
+    process loads one build).  Returns times (ms) and the results it computed."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+
+    from paper_1511_06441_gb300 import csp, synth
+    csp.LIB_PATH = lib_path
+    dev = torch.device("cuda")
+    out = {"shape": csp.build_shape(), "results": []}
+    # the cube step, traced
+    inst = synth.workload_cube(128, 1600)
+    lat = csp.Lattice(inst.extents, torch.from_numpy(inst.f1).to(dev), torch.from_numpy(inst.f2).to(dev))
+    lat.reserve(0)
+    A, B = torch.from_numpy(inst.A).to(dev), torch.from_numpy(inst.B).to(dev)
+    rec = torch.zeros(16, dtype=torch.int64, device=dev)
+    tr = torch.zeros(3 * 4096, dtype=torch.int64, device=dev)
+    s = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    e1.record(s)
+    step = 0.0
+    for M in (400, 800, 1600):
+        ts = []
+        for _ in range(4):
+            lat.solve_async(A, B, M, rec, trace_dev=tr, trace_cap=4096, stream=s, ev_begin=e0, ev_end=e1,
+                            engine="sweep")
+            s.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        r = rec.cpu().numpy()
+        out["results"].append([int(x) for x in r[1:9]])
+        step += min(ts[1:])
+    out["cube128_step_ms"] = step
+    lat.close()
+    # a quarter of the batched workload
+    insts = synth.batch_instances(512)[::4]
+    lats = [csp.Lattice(i.extents, i.f1, i.f2) for i in insts]
+    b = csp.Batch([(L, i.A, i.B, i.M) for L, i in zip(lats, insts)])
+    b.run(s)
+    torch.cuda.synchronize()
+    b.tune(b.results())
+    ts = []
+    for _ in range(2):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(s)
+        b.run(s)
+        ev[1].record(s)
+        torch.cuda.synchronize()
+        ts.append(ev[0].elapsed_time(ev[1]))
+    out["batch128_ms"] = min(ts)
+    out["results"] += [list(x.answer()) + [x.cycles, x.updates, x.status] for x in b.results()]
+    b.close()
+    return out
+
+
+def _build(shape: dict, workdir: str) -> str:
+    from paper_1511_06441_gb300 import build
+    return build.build(force=True, shape=shape, out=os.path.join(workdir, f"libcsp_{label(shape).replace('/', '_')}.so"))
+
+
+def tune(candidates=CANDIDATES, write: bool = False, parallel_builds: int = 3) -> dict:
+    workdir = tempfile.mkdtemp(prefix="csp_shapes_")
+    with cf.ThreadPoolExecutor(parallel_builds) as ex:
+        libs = list(ex.map(lambda sh: _build(sh, workdir), candidates))
+    rows = []
+    for sh, lib in zip(candidates, libs):
+        t0 = time.time()
+        p = subprocess.run([sys.executable, "-m", "paper_1511_06441_gb300.tune", "--measure", lib], cwd=ROOT,
+                           capture_output=True, text=True, timeout=900)
+        if p.returncode != 0:
+            rows.append({"shape": sh, "error": p.stderr[-400:]})
+            continue
+        m = json.loads(p.stdout.strip().splitlines()[-1])
+        m["shape"] = sh
+        m["seconds"] = round(time.time() - t0, 1)
+        rows.append(m)
+    ref = rows[0]
+    for r in rows:
+        if "error" in r:
+            r["score"] = None
+            continue
+        r["same_results"] = r["results"] == ref["results"]
+        r["score"] = r["cube128_step_ms"] / ref["cube128_step_ms"] + r["batch128_ms"] / ref["batch128_ms"]
+    ok = [r for r in rows if r.get("score") is not None and r["same_results"]]
+    best = min(ok, key=lambda r: r["score"])
+    out = {"chosen": best["shape"], "chosen_label": label(best["shape"]),
+           "gain_over_default": 2.0 / best["score"] - 1.0,
+           "measured": [{"shape": label(r["shape"]), "cube128_step_ms": r.get("cube128_step_ms"),
+                         "batch128_ms": r.get("batch128_ms"), "score": r.get("score"),
+                         "same_results": r.get("same_results"), "error": r.get("error")} for r in rows],
+           "how": "tune.py: each shape built and timed in a process of its own on one GPU; score = sum over the "
+                  "tuning workloads of time / the default shape's time",
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    try:
+        import torch
+        out["gpu"] = torch.cuda.get_device_name(0)
+    except Exception:
+        pass
+    if write:
+        from paper_1511_06441_gb300 import build
+        with open(build.SHAPE_JSON, "w") as f:
+            json.dump(out, f, indent=1)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--write", action="store_true", help="cache the chosen shape in shape.json")
+    ap.add_argument("--measure", metavar="LIB", help=argparse.SUPPRESS)  # (child process: one build)
+    args = ap.parse_args()
+    if args.measure:
+        print(json.dumps(measure(args.measure)))
+        return
+    print(json.dumps(tune(write=args.write), indent=1))
+
+
+if __name__ == "__main__":
+    main()

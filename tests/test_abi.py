@@ -64,3 +64,25 @@ def test_product_is_not_imported_by_the_oracle():
             text = open(path).read()
             assert "import paper_1511_06441_gb300" not in text and "from paper_1511_06441_gb300" not in text, path
             assert "csp_device" not in text and '#include "csp' not in text and "libcsp" not in text, path
+
+
+def test_shape_flags_from_the_cached_choice(tmp_path, monkeypatch):
+    from paper_1511_06441_gb300 import build
+    assert build.shape_flags({}) == ["-DCSP_TPB=512", "-DCSP_IPT=4", "-DCSP_NSTAGE=3", "-DCSP_MIN_CTAS_PER_SM=2",
+                                     "-DCSP_BATCH_MIN_CTAS_PER_SM=1"]
+    f = tmp_path / "shape.json"
+    f.write_text('{"chosen": {"tpb": 256, "ipt": 8, "nstage": 2, "min_ctas_per_sm": 4, "batch_min_ctas_per_sm": 2}}')
+    monkeypatch.setattr(build, "SHAPE_JSON", str(f))
+    assert build.shape_flags() == ["-DCSP_TPB=256", "-DCSP_IPT=8", "-DCSP_NSTAGE=2", "-DCSP_MIN_CTAS_PER_SM=4",
+                                   "-DCSP_BATCH_MIN_CTAS_PER_SM=2"]
+    with pytest.raises(ValueError):
+        build.shape_flags({"tpb": 0})
+
+
+def test_library_reports_its_build_shape():
+    import ctypes
+    from paper_1511_06441_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    out = (ctypes.c_int32 * 5)()
+    lib.csp_build_shape(out)
+    assert [f"-D{m}={v}" for (m, _), v in zip(build.SHAPE_KEYS.values(), out)] == build.shape_flags()

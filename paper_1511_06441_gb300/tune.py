@@ -10,7 +10,8 @@ shape.json, which build() compiles with from then on.
 Tuning workloads: the 128^3 cube solved for M = 400, 800 and 1600 with a trace (the
 benchmark's step; kernel time by CUDA events, best of three) and every fourth instance of
 the 512 mixed batch instances in one tuned batched launch.  The score of a shape is the
-sum over workloads of its time over the default shape's time.
+sum over workloads of its time over the default shape's time; a shape replaces the default
+only when its score is at least 3 % lower (smaller differences are run-to-run noise).
 """
 from __future__ import annotations
 
@@ -35,6 +36,9 @@ CANDIDATES = [
     {"tpb": 256, "ipt": 4, "nstage": 3, "min_ctas_per_sm": 4, "batch_min_ctas_per_sm": 2},
     {"tpb": 256, "ipt": 8, "nstage": 3, "min_ctas_per_sm": 4, "batch_min_ctas_per_sm": 2},
 ]
+
+
+MIN_GAIN = 0.03  # a shape replaces the default only if it is at least this much faster overall
 
 
 def label(shape: dict) -> str:
@@ -127,6 +131,8 @@ def tune(candidates=CANDIDATES, write: bool = False, parallel_builds: int = 3) -
         r["score"] = r["cube128_step_ms"] / ref["cube128_step_ms"] + r["batch128_ms"] / ref["batch128_ms"]
     ok = [r for r in rows if r.get("score") is not None and r["same_results"]]
     best = min(ok, key=lambda r: r["score"])
+    if best["score"] > (1.0 - MIN_GAIN) * 2.0:  # within noise of the default: keep the default
+        best = ref
     out = {"chosen": best["shape"], "chosen_label": label(best["shape"]),
            "gain_over_default": 2.0 / best["score"] - 1.0,
            "measured": [{"shape": label(r["shape"]), "cube128_step_ms": r.get("cube128_step_ms"),

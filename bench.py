@@ -408,7 +408,7 @@ def shape_info(csp) -> dict:
         with open(path) as f:
             t = json.load(f)
         out["tuner"] = {"chosen": t.get("chosen_label"), "gain_over_default": t.get("gain_over_default"),
-                        "measured": [[m["shape"], m.get("cube128_step_ms"), m.get("batch128_ms")]
+                        "measured": [[m["shape"], m.get("cube128_step_ms"), m.get("batch512_ms", m.get("batch128_ms"))]
                                      for m in t.get("measured", [])]}
     return out
 

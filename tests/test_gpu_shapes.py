@@ -1,8 +1,8 @@
 """Every block shape gives the same results: the library built with another shape (256
 threads x 4 flows per tile, so a 1024-flow pool chunk instead of 2048; 4 CTAs per SM)
-solves the tuning workloads (the 128^3 cube for M = 400, 800, 1600 with a trace, and 128
-mixed instances in one batched launch) with exactly the answers and counts of the default
-build.  Each build runs in a process of its own, as the shape tuner runs them."""
+solves the tuning workloads (the 128^3 cube for M = 400, 800, 1600 with a trace, and the
+512 mixed instances in one batched launch) with exactly the answers and counts of the
+default build.  Each build runs in a process of its own, as the shape tuner runs them."""
 import json
 import os
 import subprocess
@@ -30,6 +30,6 @@ def test_another_shape_gives_the_default_results():
     lib = build.build(force=True, shape=other_shape, out=os.path.join(tempfile.mkdtemp(), "libcsp_other.so"))
     other = _measure(lib)
     assert other["shape"] == other_shape and default["shape"] != other_shape
-    assert len(default["results"]) == 3 + 128
+    assert len(default["results"]) == 3 + 512
     assert other["results"] == default["results"]
     assert all(r[-1] == 0 for r in default["results"][3:])  # every batched instance solved

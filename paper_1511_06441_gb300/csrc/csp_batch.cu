@@ -41,6 +41,8 @@ struct BatchInstance {
     uint32_t *ed[2];
     int32_t *qa[2];
     int32_t *ta[2];
+    unsigned long long *pk[2];  // packed pool views (nullable)
+    unsigned int max_f1;
     uint32_t *fill[2];
     Control *ctl;
     long long *result;
@@ -73,8 +75,10 @@ __device__ __forceinline__ Params<W> batch_params(const BatchInstance &I, unsign
         P.ed[b] = I.ed[b];
         P.qa[b] = I.qa[b];
         P.ta[b] = I.ta[b];
+        P.pk[b] = I.pk[b];
         P.fill[b] = I.fill[b];
     }
+    P.max_f1 = I.max_f1;
     P.pool_cap = I.pool_cap;
     P.ctl = I.ctl;
     P.trace = nullptr;
@@ -431,6 +435,7 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
         I.nbw_in = L->nbw_in;
         I.cand_cap = (unsigned int)cand;
         I.pool_cap = (unsigned int)pool;
+        I.max_f1 = L->max_f1;
         I.nA = q[i].nA;
         I.nB = q[i].nB;
         I.M = (int)q[i].M;
@@ -465,6 +470,7 @@ csp_status csp_batch_create(const csp_query *q, int64_t n, const csp_batch_optio
             I.ed[bb] = (uint32_t *)(ws + o.pool[bb][0]);
             I.qa[bb] = (int32_t *)(ws + o.pool[bb][1]);
             I.ta[bb] = (int32_t *)(ws + o.pool[bb][2]);
+            I.pk[bb] = packed_pool(I.qa[bb], I.ta[bb], (int64_t)I.pool_cap);
             I.fill[bb] = (uint32_t *)(ws + o.fill[bb]);
         }
         I.A = (const int64_t *)(ws + o.A);

@@ -18,7 +18,10 @@
 //                     one region of cand_cap / G entries per CTA of the group
 //   pool[2]   SoA     ed = dst << 3 | direction back to the source (uint32),
 //                     qa = quality on arrival (int32), ta = arrival time (int32);
-//                     stored in chunks of TILE slots, fill[b][chunk] = slots in use
+//                     stored in chunks of TILE slots, fill[b][chunk] = slots in use.
+//                     Packed form (pk[b], where the three fit in 64 bits): one word per
+//                     flow, ed << (qb + tb) | qa << tb | (ta mod 2^tb), over the qa and ta
+//                     arrays (see PoolFmt)
 // A flow is the paper's water flow on an active (or phantom) edge: it left its source
 // at the time the source's label last improved and carries that label.
 #pragma once
@@ -135,6 +138,8 @@ struct Params {
     uint32_t *ed[2];
     int32_t *qa[2];
     int32_t *ta[2];
+    unsigned long long *pk[2];     // nullable: the packed pool over qa[b] and ta[b] (8 B per slot)
+    unsigned int max_f1;           // largest travel time of the lattice (sizes the packed time field)
     uint32_t *fill[2];             // slots in use per pool chunk (pool_cap / TILE entries)
     unsigned int pool_cap;         // slots per pool buffer, a multiple of TILE
     Control *ctl;
@@ -159,14 +164,24 @@ struct Params {
     long long pass_cap;
 };
 
+// One input stage of the sweep: a pool tile as three arrays, or (packed pool) as TILE
+// 64-bit words over qa and ta.
+struct Stage {
+    uint32_t ed[TILE];
+    int32_t qa[TILE];
+    int32_t ta[TILE];
+    __device__ __forceinline__ const unsigned long long *words() const
+    {
+        return reinterpret_cast<const unsigned long long *>(qa);
+    }
+};
+
 // Dynamic shared memory of the cycle kernel: NSTAGE input stages filled by bulk copies,
 // their barriers, and the CTA's output cursor.  The cursor word packs the chunk being
 // filled (high half) and the slots already claimed in it (low half); next_chunk is the
 // chunk allocated ahead for the warp that fills the current one.
 struct Smem {
-    uint32_t in_ed[NSTAGE][TILE];
-    int32_t in_qa[NSTAGE][TILE];
-    int32_t in_ta[NSTAGE][TILE];
+    Stage stage[NSTAGE];
     unsigned long long mbar[NSTAGE];
     unsigned long long cursor;
     uint32_t next_chunk;
@@ -392,21 +407,78 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Format of the flow pool for one solve.  Packed (tb > 0): one 64-bit word per flow,
+// ed in the high bits, the quality on arrival (1 <= qa <= M) below it in qb bits and the
+// arrival time mod 2^tb in the low tb bits, where 2^tb > max f1.  Every flow a sweep at
+// cycle time Tg reads arrives in [Tg, Tg + max f1] (it was started at a cycle time <= Tg,
+// and Tg is at most the earliest arrival in the pool), so ta = Tg + ((word - Tg) mod 2^tb).
+// The pool then moves 8 B per flow instead of 12.  Otherwise (tb = 0) the three arrays.
+// Uniform over the solve: every CTA computes it from the same Params.
+struct PoolFmt {
+    uint32_t tb;                // bits of the arrival time field; 0 = three arrays
+    uint32_t sh_e;              // tb + qb: shift of the flow word ed
+    unsigned long long qmask;   // 2^qb - 1
+};
+
+template <typename W>
+__device__ __forceinline__ PoolFmt pool_fmt(const Params<W> &P)
+{
+    PoolFmt f{0u, 0u, 0ull};
+    if (P.pk[0] == nullptr || P.pk[1] == nullptr || P.M <= 0) return f;
+    const uint32_t tb = 32u - (uint32_t)__clz((int)max(P.max_f1, 1u));
+    const uint32_t qb = 32u - (uint32_t)__clz(P.M);
+    const uint32_t eb = 64u - (uint32_t)__clzll((long long)((unsigned long long)P.V * 8ull - 1ull));
+    if (tb + qb + eb > 64u) return f;
+    f.tb = tb;
+    f.sh_e = tb + qb;
+    f.qmask = (1ull << qb) - 1ull;
+    return f;
+}
+
+__device__ __forceinline__ unsigned long long pack_flow(const PoolFmt &f, uint32_t e, int32_t q, int32_t t)
+{
+    return ((unsigned long long)e << f.sh_e) | ((unsigned long long)(uint32_t)q << f.tb) |
+           (unsigned long long)((uint32_t)t & ((1u << f.tb) - 1u));
+}
+
+__device__ __forceinline__ uint32_t packed_ed(const PoolFmt &f, unsigned long long w)
+{
+    return (uint32_t)(w >> f.sh_e);
+}
+
+__device__ __forceinline__ int32_t packed_qa(const PoolFmt &f, unsigned long long w)
+{
+    return (int32_t)((w >> f.tb) & f.qmask);
+}
+
+// Arrival time of a packed flow read by the sweep at cycle time base.
+__device__ __forceinline__ int32_t packed_ta(const PoolFmt &f, unsigned long long w, int32_t base)
+{
+    const uint32_t m = (1u << f.tb) - 1u;
+    return base + (int32_t)(((uint32_t)w - (uint32_t)base) & m);
+}
+
 // One lane: starts the bulk copy of pool chunk `tile` (buffer ib) into input stage s.
 // A chunk holds fill[ib][tile] flows; the copy is rounded up to 16 bytes and the slots
 // past the fill are ignored.  An empty chunk completes the stage without a copy.
 template <typename W>
-__device__ __forceinline__ void issue_tile(const Params<W> &P, Smem &sm, int s, int ib, uint32_t tile)
+__device__ __forceinline__ void issue_tile(const Params<W> &P, const PoolFmt &f, Smem &sm, int s, int ib, uint32_t tile)
 {
     const uint32_t n = min((uint32_t)TILE, __ldcg(P.fill[ib] + tile));
     const uint32_t start = tile * (uint32_t)TILE;
-    const uint32_t bytes = ((n + 3u) & ~3u) * 4u;
     sm.stage_fill[s] = n;
+    if (f.tb) {
+        const uint32_t bytes = ((n + 1u) & ~1u) * 8u;
+        mbar_expect_tx(&sm.mbar[s], bytes);
+        if (bytes) bulk_g2s(sm.stage[s].qa, P.pk[ib] + start, bytes, &sm.mbar[s]);
+        return;
+    }
+    const uint32_t bytes = ((n + 3u) & ~3u) * 4u;
     mbar_expect_tx(&sm.mbar[s], 3u * bytes);
     if (bytes) {
-        bulk_g2s(sm.in_ed[s], P.ed[ib] + start, bytes, &sm.mbar[s]);
-        bulk_g2s(sm.in_qa[s], P.qa[ib] + start, bytes, &sm.mbar[s]);
-        bulk_g2s(sm.in_ta[s], P.ta[ib] + start, bytes, &sm.mbar[s]);
+        bulk_g2s(sm.stage[s].ed, P.ed[ib] + start, bytes, &sm.mbar[s]);
+        bulk_g2s(sm.stage[s].qa, P.qa[ib] + start, bytes, &sm.mbar[s]);
+        bulk_g2s(sm.stage[s].ta, P.ta[ib] + start, bytes, &sm.mbar[s]);
     }
 }
 
@@ -605,17 +677,47 @@ __device__ __forceinline__ void cursor_close(const Params<W> &P, Smem &sm, int o
     }
 }
 
+// 64-bit global store with an L2 cache policy.
+__device__ __forceinline__ void st_policy64(unsigned long long *a, unsigned long long v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(a), "l"(v), "l"(pol) : "memory");
+}
+
 // Writes one flow to slot p of a span (evict-first in L2), or records the overflow.
 template <typename W>
-__device__ __forceinline__ void put_flow(const Params<W> &P, int ob, Counters *C, const Span &sp, uint32_t p,
-                                         uint32_t e, int32_t q, int32_t t)
+__device__ __forceinline__ void put_flow(const Params<W> &P, const PoolFmt &f, int ob, Counters *C, const Span &sp,
+                                         uint32_t p, uint32_t e, int32_t q, int32_t t)
 {
     uint32_t idx;
     if (span_slot(sp, p, idx)) {
         const unsigned long long pol = policy_evict_first();
-        st_policy(P.ed[ob] + idx, e, pol);
-        st_policy(reinterpret_cast<uint32_t *>(P.qa[ob]) + idx, (uint32_t)q, pol);
-        st_policy(reinterpret_cast<uint32_t *>(P.ta[ob]) + idx, (uint32_t)t, pol);
+        if (f.tb) {
+            st_policy64(P.pk[ob] + idx, pack_flow(f, e, q, t), pol);
+        } else {
+            st_policy(P.ed[ob] + idx, e, pol);
+            st_policy(reinterpret_cast<uint32_t *>(P.qa[ob]) + idx, (uint32_t)q, pol);
+            st_policy(reinterpret_cast<uint32_t *>(P.ta[ob]) + idx, (uint32_t)t, pol);
+        }
+    } else {
+        atomicExch(&C->overflow, 1u);
+    }
+}
+
+// A survivor of the sweep, copied from input stage s slot j to slot p of a span.
+template <typename W>
+__device__ __forceinline__ void copy_flow(const Params<W> &P, const PoolFmt &f, int ob, Counters *C, const Span &sp,
+                                          uint32_t p, const Stage &in, uint32_t j, uint32_t e)
+{
+    uint32_t idx;
+    if (span_slot(sp, p, idx)) {
+        const unsigned long long pol = policy_evict_first();
+        if (f.tb) {
+            st_policy64(P.pk[ob] + idx, in.words()[j], pol);  // (ta mod 2^tb is unchanged)
+        } else {
+            st_policy(P.ed[ob] + idx, e, pol);
+            st_policy(reinterpret_cast<uint32_t *>(P.qa[ob]) + idx, (uint32_t)in.qa[j], pol);
+            st_policy(reinterpret_cast<uint32_t *>(P.ta[ob]) + idx, (uint32_t)in.ta[j], pol);
+        }
     } else {
         atomicExch(&C->overflow, 1u);
     }
@@ -644,10 +746,13 @@ __device__ __forceinline__ void put_flow(const Params<W> &P, int ob, Counters *C
 
 template <int D, typename W, bool TRACE>
 __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int ib, uint32_t n_tiles, int Tg,
-                                       uint32_t stamp, Counters *C, LocalStats &st, Smem &sm, uint32_t (&parity)[NSTAGE],
-                                       uint32_t cand_base, uint32_t cand_cap)
+                                       int tbase, uint32_t stamp, Counters *C, LocalStats &st, Smem &sm,
+                                       uint32_t (&parity)[NSTAGE], uint32_t cand_base, uint32_t cand_cap)
 {
+    // tbase: a time no later than any arrival in the pool and within max f1 of all of them
+    // (the cycle time; decodes the packed arrival times)
     const int ob = ib ^ 1;
+    const PoolFmt fmt = pool_fmt(P);
     const uint32_t n_chunks = P.pool_cap / (uint32_t)TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
@@ -662,7 +767,7 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
         sm.fail = 0;
         if (g.rank < n_tiles) fence_proxy_async_global();  // pool written by ordinary stores in the previous pass
         for (int s = 0; s < NSTAGE; s++)
-            if (g.rank + s * G < n_tiles) issue_tile(P, sm, s, ib, g.rank + s * G);
+            if (g.rank + s * G < n_tiles) issue_tile(P, fmt, sm, s, ib, g.rank + s * G);
     }
     __syncthreads();
     bool ok = true;
@@ -680,7 +785,7 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
             const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
-            e[i] = j < nfill ? sm.in_ed[s][j] : 0u;
+            e[i] = j >= nfill ? 0u : fmt.tb ? packed_ed(fmt, sm.stage[s].words()[j]) : sm.stage[s].ed[j];
         }
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
@@ -692,7 +797,7 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
             const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
-            const int32_t q = j < nfill ? sm.in_qa[s][j] : 0;
+            const int32_t q = j >= nfill ? 0 : fmt.tb ? packed_qa(fmt, sm.stage[s].words()[j]) : sm.stage[s].qa[j];
             bool keep = false, arr = false;
             const bool live = q > L[i];  // (padding has q = 0 <= INT_MAX)
             if (TRACE && live) {  // the source is active in this pass (a plain store: every writer agrees)
@@ -702,7 +807,7 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
             if (live) {
                 st.live++;
                 const uint32_t dst = e[i] >> 3;
-                const int32_t t = sm.in_ta[s][j];
+                const int32_t t = fmt.tb ? packed_ta(fmt, sm.stage[s].words()[j], tbase) : sm.stage[s].ta[j];
                 if (t == Tg) {
                     const unsigned long long key =
                         ((unsigned long long)(uint32_t)q << 32) | arrival_code<D>(P, e[i]);
@@ -746,7 +851,7 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
             for (int i = 0; i < IPT; i++) {
                 if ((bk[i] >> lane) & 1u) {
                     const uint32_t j = (uint32_t)(warp * (32 * IPT) + i * 32 + lane);
-                    put_flow(P, ob, C, sp, p + __popc(bk[i] & lt), e[i], sm.in_qa[s][j], sm.in_ta[s][j]);
+                    copy_flow(P, fmt, ob, C, sp, p + __popc(bk[i] & lt), sm.stage[s], j, e[i]);
                 }
                 p += __popc(bk[i]);
             }
@@ -762,7 +867,7 @@ __device__ CSP_PHASE_INLINE bool sweep(const Params<W> &P, const Group &g, int i
                 if (tile + NSTAGE * G < n_tiles) {
                     fence_proxy_async_global();  // (this lane's view of the pool written last pass)
                     fence_proxy_async_smem();
-                    issue_tile(P, sm, s, ib, tile + NSTAGE * G);
+                    issue_tile(P, fmt, sm, s, ib, tile + NSTAGE * G);
                 }
             }
         }
@@ -822,7 +927,7 @@ __device__ __forceinline__ uint32_t launch_mask(const EdgeRecord<W, D> &r, int L
 // consecutive slots (so the flows of one source stay together for the trace count of
 // later sweeps).
 template <typename W, int D>
-__device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters *C, Smem &sm, uint32_t v, int Lv,
+__device__ __forceinline__ void emit_flows(const Params<W> &P, const PoolFmt &f, int ob, Counters *C, Smem &sm, uint32_t v, int Lv,
                                            const EdgeRecord<W, D> &r, uint32_t mask, int Time, LocalStats &st)
 {
     const int lane = threadIdx.x & 31;
@@ -842,7 +947,7 @@ __device__ __forceinline__ void emit_flows(const Params<W> &P, int ob, Counters 
     for (int dir = 0; dir < nslots(D); dir++)
         if (mask & (1u << dir)) {
             const int t = Time + r.f1(dir);
-            put_flow(P, ob, C, sp, p, flow_word<D>(P, v, dir), Lv - r.f2(dir), t);
+            put_flow(P, f, ob, C, sp, p, flow_word<D>(P, v, dir), Lv - r.f2(dir), t);
             p++;
             st.min_ta = min(st.min_ta, t);
             st.launched++;
@@ -862,6 +967,7 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
                                         int Time, uint32_t stamp, Counters *C, LocalStats &st, Smem &sm)
 {
     const uint32_t V = (uint32_t)P.V;
+    const PoolFmt fmt = pool_fmt(P);
     if (TRACE) {  // active vertices: stamped by this pass's sweep (16-byte loads, 4 vertices each)
         const uint4 *st4 = reinterpret_cast<const uint4 *>(P.src_stamp);
         const uint32_t n4 = (V + 3) / 4;
@@ -922,7 +1028,7 @@ __device__ CSP_PHASE_INLINE void launch(const Params<W> &P, const Group &g, int 
                 if (won && i < P.log_cap) P.log[i] = make_uint2(v, code);
             }
         }
-        emit_flows<W, D>(P, ob, C, sm, v, Lv, r, mask, Time, st);
+        emit_flows<W, D>(P, fmt, ob, C, sm, v, Lv, r, mask, Time, st);
     }
 }
 
@@ -933,6 +1039,7 @@ __device__ CSP_PHASE_INLINE void seed(const Params<W> &P, const Group &g, uint32
                                       Smem &sm)
 {
     const uint32_t V = (uint32_t)P.V;
+    const PoolFmt fmt = pool_fmt(P);
     const uint32_t wbase = g.rank * TPB + (threadIdx.x >> 5) * 32u;
     for (uint32_t base = wbase; base < n_src; base += g.size * TPB) {
         const uint32_t j = base + (threadIdx.x & 31);
@@ -945,7 +1052,7 @@ __device__ CSP_PHASE_INLINE void seed(const Params<W> &P, const Group &g, uint32
             neighbour_labels<D>(P, V, v, Lw);
             mask = launch_mask<W, D>(r, P.M, Lw);
         }
-        emit_flows<W, D>(P, 0, C, sm, v, P.M, r, mask, 0, st);
+        emit_flows<W, D>(P, fmt, 0, C, sm, v, P.M, r, mask, 0, st);
     }
 }
 
@@ -1092,7 +1199,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
             Counters *C = &ctl->cnt[ob];
             LocalStats sa{0, 0, 0, 0, 0, 0, 0, INT_MAX};
             if (threadIdx.x == 0) cursor_open(sm);
-            if (!sweep<D, W, TRACE>(P, g, ib, n_tiles, Tg, (uint32_t)pass, C, sa, sm, parity, cand_base, cand_cta)) {
+            if (!sweep<D, W, TRACE>(P, g, ib, n_tiles, Tg, Tg, (uint32_t)pass, C, sa, sm, parity, cand_base, cand_cta)) {
                 status = ST_BARRIER;
                 goto finish;
             }
@@ -1136,7 +1243,7 @@ __device__ void run_solve(const Params<W> &P, const Group &g, Smem &sm, uint32_t
                         LocalStats sc{0, 0, 0, 0, 0, 0, 0, INT_MAX};
                         const uint32_t nt = min(c.chunks, n_chunks);
                         if (threadIdx.x == 0) cursor_open(sm);
-                        if (!sweep<D, W, TRACE>(P, g, ob, nt, -1, (uint32_t)pass + 1u, &ctl->cnt[ib], sc, sm, parity, cand_base,
+                        if (!sweep<D, W, TRACE>(P, g, ob, nt, -1, Time, (uint32_t)pass + 1u, &ctl->cnt[ib], sc, sm, parity, cand_base,
                                                 cand_cta)) {
                             status = ST_BARRIER;
                             goto finish;

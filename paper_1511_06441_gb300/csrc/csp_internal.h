@@ -24,6 +24,16 @@ extern thread_local std::string g_last_error;
 inline int record_bytes(int d, int wbytes) { return wbytes * 2 * csp::nslots(d) <= 16 ? 16 : 32; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The packed view of a pool buffer (one 64-bit word per slot) over its qa and ta arrays, when
+// ta starts right after qa's pool_cap + POOL_PAD entries (so the words of pool_cap + POOL_PAD / 2
+// slots fit) and qa is 16-byte aligned for bulk copies; null otherwise (the kernel then keeps
+// the three arrays).
+inline unsigned long long *packed_pool(int32_t *qa, int32_t *ta, int64_t pool_cap)
+{
+    const bool adjacent = (char *)ta == (char *)qa + (size_t)(pool_cap + csp::POOL_PAD) * 4;
+    return adjacent && ((uintptr_t)qa % 16) == 0 ? reinterpret_cast<unsigned long long *>(qa) : nullptr;
+}
+
 struct csp_event_ws;
 
 struct csp_lattice {

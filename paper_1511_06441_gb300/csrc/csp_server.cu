@@ -77,6 +77,7 @@ struct GroupSlot {
     uint32_t *ed[2];
     int32_t *qa[2];
     int32_t *ta[2];
+    unsigned long long *pk[2];  // packed pool views (nullable)
     uint32_t *fill[2];
     Control *ctl;
     long long *result;  // device copy of the current query's result
@@ -89,6 +90,7 @@ struct ServerArgs {
     const uint32_t *nbw, *nbw_in;  // general graphs: the out- and in-edge tables (null on a lattice)
     long long V;
     int stride[4];
+    unsigned int max_f1;       // largest travel time of the lattice
     const GroupSlot *slots;    // [groups] narrow slots, then the wide slot (whole grid)
     int group_ctas, groups;
     unsigned long long *head;  // device: next ring position to claim
@@ -120,8 +122,10 @@ __device__ void slot_params(Params<W> &P, const ServerArgs &S, const GroupSlot &
         P.ed[b] = slot.ed[b];
         P.qa[b] = slot.qa[b];
         P.ta[b] = slot.ta[b];
+        P.pk[b] = slot.pk[b];
         P.fill[b] = slot.fill[b];
     }
+    P.max_f1 = S.max_f1;
     P.pool_cap = slot.pool_cap;
     P.ctl = slot.ctl;
     P.result_dev = slot.result;
@@ -453,6 +457,7 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
             g.ed[q] = (uint32_t *)(b + y.pool_o[q][0]);
             g.qa[q] = (int32_t *)(b + y.pool_o[q][1]);
             g.ta[q] = (int32_t *)(b + y.pool_o[q][2]);
+            g.pk[q] = packed_pool(g.qa[q], g.ta[q], y.pool);
             g.fill[q] = (uint32_t *)(b + y.fill[q]);
         }
         g.ctl = (Control *)(b + y.ctl);
@@ -481,6 +486,7 @@ csp_status csp_server_create(csp_lattice *L, const csp_server_options *opt, csp_
         a.nbw_in = L->nbw_in;
         a.V = V;
         for (int k = 0; k < 4; k++) a.stride[k] = L->stride[k];
+        a.max_f1 = L->max_f1;
         a.slots = s->d_slots;
         a.group_ctas = gc;
         a.groups = groups;

@@ -510,8 +510,10 @@ csp_status enqueue_solve(csp_lattice *L, const int64_t *A_dev, int64_t nA, const
             P.ed[b] = L->ed[b];
             P.qa[b] = L->qa[b];
             P.ta[b] = L->ta[b];
+            P.pk[b] = packed_pool(L->qa[b], L->ta[b], L->pool_cap);
             P.fill[b] = L->fill[b];
         }
+        P.max_f1 = L->max_f1;
         P.pool_cap = (unsigned int)L->pool_cap;
         P.ctl = L->ctl;
         P.trace = trace_dev;
@@ -1251,8 +1253,10 @@ extern "C" csp_status csp_solve_static(int d, const int64_t *extents, const void
             P.ed[q] = (uint32_t *)(b + o_pool[q][0]);
             P.qa[q] = (int32_t *)(b + o_pool[q][1]);
             P.ta[q] = (int32_t *)(b + o_pool[q][2]);
+            P.pk[q] = packed_pool(P.qa[q], P.ta[q], (int64_t)pool_cap);
             P.fill[q] = (uint32_t *)(b + o_fill[q]);
         }
+        P.max_f1 = weight_bytes == 1 ? 255u : 65535u;  // (the weights are not scanned here: their type's bound)
         P.pool_cap = (unsigned int)pool_cap;
         P.ctl = ctl;
         P.trace = nullptr;

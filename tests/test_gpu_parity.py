@@ -163,6 +163,22 @@ def test_f2_zero_first_passage_at_size(csp, ext):
     lat.close()
 
 
+@pytest.mark.parametrize("M", [2**31 - 2, 2**20, 140000])
+def test_both_pool_formats(csp, M):
+    # A path of 16,512 vertices with travel times up to 40,000 (16-bit weights).  With
+    # M = 2^31 - 2 the flow word (18 bits), the quality (31 bits) and the arrival time (16
+    # bits) do not fit one 64-bit word and the pool keeps three arrays; with M = 2^20 they
+    # fit and each flow is one packed word.  Arrival times reach 3.3e8, far beyond the
+    # 16-bit time field of the packed form; at M = 140,000 the only path is too heavy.
+    ext = [16512]
+    f1, f2 = synth.uniform_weights(ext, 1, 40000, 123, dtype=np.uint16)
+    f2 = (f2 % 16 + 1).astype(np.uint16)
+    assert int(f1[:16511].max()) >= 1 << 15
+    inst = synth.Instance(ext, f1, f2, np.array([0], np.int64), np.array([16511], np.int64), M, "path16512")
+    got, want = _run_pair(csp, inst)
+    assert (got.F1 == -1) == (M == 140000)
+
+
 def test_edge_cases(csp):
     ext = [6, 5]
     f1, f2 = synth.uniform_weights(ext, 1, 5, 3)

@@ -470,7 +470,7 @@ def bench_engines(csp, lat, A, B, stream, trace, trace_cap, rec, sweep_out, swee
             "event_updates_per_s": upd / (sum(ms) / 1e3), "event_vs_sweep": sum(sweep_avg) / sum(ms),
             "default_form": lat.default_engine(),
             "note": "event form: per-edge queues and a calendar of arrival times (CSP_OPT_EVENT); the default "
-                    "form for this lattice is the sweep (mean f1 8.5 < 96)"}
+                    "form for this lattice is the sweep (mean f1 8.5 < 64)"}
 
 
 def bench_anticorrelated(csp, synth, no_cpu=False):

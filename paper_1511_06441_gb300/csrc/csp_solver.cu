@@ -396,13 +396,14 @@ int64_t default_pool_cap(const csp_lattice *L)
 // The default form of the cycle loop for a handle.  The event form visits a flow when it
 // starts, arrives or is removed; the sweep visits every flow in flight in every cycle, so
 // the event form pays off when flows stay in flight over many cycles: measured on one
-// GB300, 1.21x and 1.25x faster at mean travel times of 128 and 256 (1024^2 lattices with
-// f1 ~ U{1..255} and U{1..511}), 0.80x at 32.5 (f1 ~ U{1..64}), 0.31x on the 128^3 cube
-// (f1 ~ U{1..16}) and 0.27-0.77x on the anti-correlated lattices (geometric f1, mean 10).
-// Its per-edge queues are larger than the sweep's flow pool, so where cycles are dense it
-// spends its time on random accesses that miss L2.  Rule: the event form when the mean f1
-// over directed edges is at least kEventMeanF1 and it supports the handle.
-constexpr unsigned long long kEventMeanF1 = 96;
+// GB300 (1024^2 lattices, f2 ~ U{1..16}, M = 12288), 0.81x the sweep's speed at a mean
+// travel time of 32.5 (f1 ~ U{1..64}), 1.04x at 64.5, 1.12x at 96, 1.18x at 128 and 1.21x
+// at 256 (f1 up to 511); 0.34x on the 128^3 cube (f1 ~ U{1..16}) and 0.27-0.77x on the
+// anti-correlated lattices (geometric f1, mean 10).  Its per-edge queues are larger than the
+// sweep's flow pool, so where cycles are dense it spends its time on random accesses that
+// miss L2.  Rule: the event form when the mean f1 over directed edges is at least
+// kEventMeanF1 (just above the crossover, near 59) and it supports the handle.
+constexpr unsigned long long kEventMeanF1 = 64;
 
 bool event_preferred(const csp_lattice *L)
 {

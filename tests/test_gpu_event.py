@@ -367,8 +367,9 @@ def test_fast_reconstruction_tiny(csp, seed):
 
 
 def test_default_engine_follows_mean_travel_time(csp):
-    # long travel times (mean f1 >= 96 over directed edges): the event form by default; the
-    # 1-16 cube: the sweep.  Either way the solve equals the oracle.
+    # long travel times (mean f1 >= 64 over directed edges): the event form by default; the
+    # 1-16 cube and travel times 1-64 (mean 32.5): the sweep.  Either way the solve equals the
+    # oracle.
     ext = [90, 70]
     f1, f2 = synth.uniform_weights(ext, 1, 255, 91, dtype=np.uint16)
     f2 = (f2 % 16 + 1).astype(np.uint16)
@@ -382,5 +383,9 @@ def test_default_engine_follows_mean_travel_time(csp):
     lat.close()
     cube = synth.workload_cube(20, 260)
     lat = csp.Lattice(cube.extents, cube.f1, cube.f2)
+    assert lat.default_engine() == "sweep"
+    lat.close()
+    f1, f2 = synth.uniform_weights(ext, 1, 64, 92)
+    lat = csp.Lattice(ext, f1, f2)
     assert lat.default_engine() == "sweep"
     lat.close()
